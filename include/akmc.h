@@ -1,0 +1,175 @@
+/*
+ * akmc.h -- C ABI of the GB300 (sm_103a) vacancy AKMC library (libakmc.so).
+ *
+ * Rejection-free atomistic kinetic Monte Carlo of vacancy-mediated diffusion
+ * on periodic bcc Fe-Cu-Ni-Mn voxels: the classical AKMC that AtomWorld
+ * (arXiv 2604.24091) accelerates.  Per event and voxel it enumerates and
+ * rates every 1nn migration of every vacancy (Sec. "Compute-Centric
+ * Reformulation": all migration directions of each vacancy), keeps the rate
+ * sums in a per-voxel binary tree, selects one event in proportion to its
+ * rate from a counter-based Philox stream, applies the swap and advances a
+ * compensated float64 clock by -ln(u)/Gamma_tot (time step inversely
+ * proportional to the total rate, Sec. "Current State of the Art").  Rates
+ * are Arrhenius (Eq. 8) with a KRA barrier; hops into a vacancy are masked
+ * out (the admissibility mask of Eq. 1) and all events of a voxel compete
+ * in one global selection (Eq. 2).  Voxels are independent periodic boxes
+ * (Sec. "Mesoscopic Voxel-Parallel Formulation"), which is the batch axis.
+ *
+ * Conventions
+ *  - Lattice: site s = ((z*L + y)*L + x)*2 + b, x,y,z in [0,L) cells, b = 0
+ *    corner / 1 body centre; half-unit coordinates (2x+b, 2y+b, 2z+b) mod 2L.
+ *    Species codes (uint8): Fe 0, Cu 1, Ni 2, Mn 3, vacancy 4.
+ *  - Hop direction of a vacancy: dir = (dx<0) + 2(dy<0) + 4(dz<0) for the
+ *    1nn vector (+-1,+-1,+-1) in half units; event index = 8*slot + dir.
+ *  - Device memory is owned by the caller: every device buffer the library
+ *    uses lives in one caller-allocated workspace (for example a torch uint8
+ *    tensor).  The library never calls cudaMalloc/cudaFree; it allocates only
+ *    small host-side bookkeeping (including pinned staging for targets).
+ *  - Streams are passed as opaque pointers (a cudaStream_t; NULL = legacy
+ *    default stream).  Calls are stream-ordered and return without waiting,
+ *    except akmc_read_state, akmc_sync_status and akmc_cluster_hist, which
+ *    synchronise the given stream.
+ *  - Errors: every call returns an akmc_status; the text of the last error
+ *    of the calling thread is available from akmc_last_error().  Per-voxel
+ *    device status words report trapped voxels and numeric errors.  The
+ *    library never aborts the process.
+ */
+#ifndef AKMC_H
+#define AKMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct akmc_batch akmc_batch;   /* opaque, owned by the library */
+typedef void* akmc_stream;              /* a cudaStream_t */
+
+typedef enum {
+    AKMC_OK = 0,
+    AKMC_EINVAL = 1,    /* invalid argument or descriptor                         */
+    AKMC_ENOMEM = 2,    /* workspace smaller than akmc_workspace_bytes()          */
+    AKMC_ECUDA = 3,     /* a CUDA runtime call failed (message in last_error)     */
+    AKMC_ETIMEOUT = 4,  /* reserved: a bounded device wait gave up                */
+    AKMC_ETRAPPED = 5,  /* voxel total rate is 0: no admissible event             */
+    AKMC_ENUMERIC = 6   /* density outside the embedding table, or NaN/Inf rate   */
+} akmc_status;
+
+enum { AKMC_PAIR = 0, AKMC_EAM = 1 };          /* energy model            */
+enum { AKMC_FP64 = 0, AKMC_SPLIT = 1 };        /* EAM arithmetic          */
+
+/* One voxel.  Species counts are n_s = floor(frac_s * 2L^3 + 0.5) for
+ * s = Cu, Ni, Mn; n_vac vacancies; Fe is the balance.  Placement draws sites
+ * from the Philox placement stream (key = seed, counter word3 has its top
+ * bit set) by sequential rejection: vacancies first (slot = placement order),
+ * then Cu, Ni, Mn.  Requirements: pair model L >= 3, EAM L >= 4, L <= 1024,
+ * 2L^3 < 2^31, 1 <= n_vac <= 256, T > 0. */
+typedef struct {
+    int32_t L;
+    int32_t n_vac;
+    double frac[3];
+    double T;              /* K */
+    int32_t model;         /* AKMC_PAIR or AKMC_EAM */
+    int32_t precision;     /* EAM only: AKMC_FP64 or AKMC_SPLIT (FP32 embedding, exact fixed-point + FP64 assembly) */
+    uint64_t seed;         /* Philox key */
+    uint64_t uid;          /* voxel id: Philox counter words 2-3 (event stream independent of batching) */
+} akmc_voxel_desc;
+
+/* Energy model shared by all voxels of a batch (host pointers; copied at create).
+ * Pair model: E = 1/2 sum_i sum_{j in N1(i)} eps1[s_i][s_j] + 1/2 sum_i sum_{j in N2(i)} eps2[s_i][s_j],
+ *   species order Fe,Cu,Ni,Mn,V; every eps must be a multiple of 2^-24 eV with
+ *   |eps| < 4 eV (exact sums).  Hop dE is the exact change of E.
+ * EAM: E = sum_{i != V} [F_{s_i}(rho_i) + 1/2 sum_{j in S(i), j != V} phi_{s_i s_j}(r_ij)],
+ *   rho_i = sum_{j in S(i), j != V} f_{s_j}(r_ij), S = the 58 sites within r_cut.
+ *   phi/f are tabulated on r_k = k*r_cut/(n_r-1), F on rho_k = k*rho_h
+ *   (rho_h a power of two in [2^-24, 1]), each as (value, derivative) pairs
+ *   evaluated by cubic Hermite interpolation.  f at the 5 shell radii is
+ *   rounded to a multiple of 2^-24 (densities are exact fixed-point sums).
+ * Barrier Ea = max(0, dE, E0[A] + dE/2) for the jumping species A;
+ * rate = nu * exp(-Ea/(kB*T)), kB = 8.617333262e-5 eV/K. */
+typedef struct {
+    double eps1[25], eps2[25];
+    double E0[4];
+    double nu;
+    double a;              /* lattice constant, Angstrom */
+    double r_cut;          /* EAM cutoff, Angstrom (must lie between the 5th and 6th shells) */
+    int32_t n_r, n_rho;    /* table lengths (0 when no voxel uses EAM) */
+    double rho_h;
+    const double* phi_tab; /* [10][n_r][2], pair index of a<=b: a*(7-a)/2 + b */
+    const double* f_tab;   /* [4][n_r][2] */
+    const double* F_tab;   /* [4][n_rho][2] */
+} akmc_model;
+
+/* Host-side view of one voxel; any pointer may be NULL (not copied). */
+typedef struct {
+    uint8_t* species;      /* [2L^3]                                          */
+    int32_t* vac_pos;      /* [n_vac] site of each vacancy slot               */
+    int32_t* vac_disp;     /* [3 n_vac] unwrapped displacement, half units    */
+    double* rates;         /* [8 n_vac] hop rates (1/s), event order          */
+    double* dE;            /* [8 n_vac] hop energy changes (eV), 0 into a vacancy */
+    int32_t* event_log;    /* [event_log_capacity] ring: entry n % cap = 8*slot+dir of event n */
+    double t_hi, t_lo;     /* simulated time = t_hi + t_lo (s)                */
+    uint64_t n_events;     /* events executed so far (Philox event counter)   */
+    int32_t status;        /* akmc_status of the voxel                        */
+    int32_t L, n_vac;
+} akmc_state;
+
+/* Bytes of device workspace a batch needs (0 and last_error set if the
+ * descriptors or model are invalid).  Pure host computation. */
+size_t akmc_workspace_bytes(const akmc_voxel_desc* descs, int32_t n_voxels,
+                            const akmc_model* model, int32_t event_log_capacity);
+
+/* Lay the batch out in dev_workspace (>= akmc_workspace_bytes), upload the
+ * model and descriptors, place species on the device (a1) and build densities,
+ * rates and rate trees (akmc_compute_rates).  Stream-ordered. */
+akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n_voxels,
+                              const akmc_model* model, int32_t event_log_capacity,
+                              void* dev_workspace, size_t workspace_bytes,
+                              akmc_stream stream, akmc_batch** out);
+
+/* Full rebuild of every voxel: EAM densities from the lattice (fixed-point,
+ * exact), then the 8 rates of every vacancy and the rate trees. */
+akmc_status akmc_compute_rates(akmc_batch* batch, akmc_stream stream);
+
+/* Run n_events[v] further events on every voxel v (host array of n_voxels
+ * entries; copied before return).  One persistent launch steps all voxels;
+ * a voxel stops early when trapped or on a numeric error.  Results do not
+ * depend on the batch composition or launch shape: each voxel's stream is
+ * Philox(seed, (n, uid)). */
+akmc_status akmc_step_n(akmc_batch* batch, const uint64_t* n_events, akmc_stream stream);
+
+/* Copy one voxel's state to host memory; synchronises the stream. */
+akmc_status akmc_read_state(akmc_batch* batch, int32_t voxel, akmc_state* out, akmc_stream stream);
+
+/* Replace one voxel's lattice (same L and n_vac), clock and event counter;
+ * displacements restart at 0.  The next akmc_step_n or akmc_compute_rates
+ * rebuilds rates first.  Host inputs are copied before return. */
+akmc_status akmc_load_state(akmc_batch* batch, int32_t voxel, const uint8_t* species,
+                            const int32_t* vac_pos, double t_hi, double t_lo,
+                            uint64_t n_events, akmc_stream stream);
+
+/* Synchronise the stream and report voxel statuses: per_voxel (nullable,
+ * n_voxels entries); returns AKMC_OK if every voxel is OK, else the status
+ * of the lowest-indexed voxel that is not. */
+akmc_status akmc_sync_status(akmc_batch* batch, akmc_stream stream, int32_t* per_voxel);
+
+/* Cu cluster size histogram of one voxel: connected components of Cu under
+ * 1nn+2nn (mode 0) or 1nn (mode 1) adjacency; bins {1,2,3,4,5-9,10-19,
+ * 20-49,>=50}.  Uses scratch memory inside the workspace; synchronises. */
+akmc_status akmc_cluster_hist(akmc_batch* batch, int32_t voxel, int32_t mode,
+                              int64_t hist[8], akmc_stream stream);
+
+/* Launch shape of akmc_step_n: warps per voxel-CTA (1, 2, 4 or 8) and CTAs
+ * per SM (0 = as many as fit).  Results are identical for every shape. */
+akmc_status akmc_set_launch(akmc_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm);
+
+int32_t akmc_n_voxels(const akmc_batch* batch);
+void akmc_destroy_batch(akmc_batch* batch);      /* never frees caller memory */
+const char* akmc_last_error(void);               /* thread-local, never NULL */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AKMC_H */

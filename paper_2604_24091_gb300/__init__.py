@@ -1,0 +1,7 @@
+"""GB300-native (sm_103a) rejection-free vacancy AKMC on bcc Fe-Cu-Ni-Mn.
+
+The compute path is libakmc.so (CUDA kernels behind the C ABI in
+include/akmc.h); this package only marshals arguments to it.
+"""
+from .akmc import (AkmcError, Batch, load_library, last_error, workspace_bytes,  # noqa: F401
+                   OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ETRAPPED, ENUMERIC, STATUS_NAMES)

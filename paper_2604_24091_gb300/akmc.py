@@ -1,0 +1,234 @@
+"""ctypes binding of libakmc (include/akmc.h): argument marshalling only.
+
+PyTorch provides the device workspace and the stream; every step of the
+AKMC path runs in the library's CUDA kernels.  There is no fallback: if the
+compiled library or a CUDA device is missing, the constructor raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libakmc.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ETRAPPED, ENUMERIC = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ETRAPPED", 6: "ENUMERIC"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AkmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class VoxelDescC(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("n_vac", ctypes.c_int32), ("frac", ctypes.c_double * 3),
+                ("T", ctypes.c_double), ("model", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("uid", ctypes.c_uint64)]
+
+
+class ModelC(ctypes.Structure):
+    _fields_ = [("eps1", ctypes.c_double * 25), ("eps2", ctypes.c_double * 25),
+                ("E0", ctypes.c_double * 4), ("nu", ctypes.c_double), ("a", ctypes.c_double),
+                ("r_cut", ctypes.c_double), ("n_r", ctypes.c_int32), ("n_rho", ctypes.c_int32),
+                ("rho_h", ctypes.c_double), ("phi_tab", ctypes.c_void_p), ("f_tab", ctypes.c_void_p),
+                ("F_tab", ctypes.c_void_p)]
+
+
+class StateC(ctypes.Structure):
+    _fields_ = [("species", ctypes.c_void_p), ("vac_pos", ctypes.c_void_p), ("vac_disp", ctypes.c_void_p),
+                ("rates", ctypes.c_void_p), ("dE", ctypes.c_void_p), ("event_log", ctypes.c_void_p),
+                ("t_hi", ctypes.c_double), ("t_lo", ctypes.c_double), ("n_events", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("L", ctypes.c_int32), ("n_vac", ctypes.c_int32)]
+
+
+def load_library():
+    """Load libakmc.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libakmc.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, U64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+        sig = {
+            "akmc_workspace_bytes": (SZ, [P, I32, P, I32]),
+            "akmc_create_batch": (I32, [P, I32, P, I32, P, SZ, P, ctypes.POINTER(P)]),
+            "akmc_compute_rates": (I32, [P, P]),
+            "akmc_step_n": (I32, [P, P, P]),
+            "akmc_read_state": (I32, [P, I32, ctypes.POINTER(StateC), P]),
+            "akmc_load_state": (I32, [P, I32, P, P, ctypes.c_double, ctypes.c_double, U64, P]),
+            "akmc_sync_status": (I32, [P, P, P]),
+            "akmc_cluster_hist": (I32, [P, I32, I32, P, P]),
+            "akmc_set_launch": (I32, [P, I32, I32]),
+            "akmc_n_voxels": (I32, [P]),
+            "akmc_destroy_batch": (None, [P]),
+            "akmc_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def last_error() -> str:
+    return load_library().akmc_last_error().decode()
+
+
+def _check(st):
+    if st != OK:
+        raise AkmcError(st, last_error())
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def make_descs(descs) -> ctypes.Array:
+    arr = (VoxelDescC * len(descs))()
+    for i, d in enumerate(descs):
+        c = arr[i]
+        c.L, c.n_vac = int(d.L), int(d.n_vac)
+        fr = list(d.frac) + [0.0] * (3 - len(d.frac))
+        c.frac[:] = [float(x) for x in fr[:3]]
+        c.T, c.model, c.precision = float(d.T), int(d.model), int(d.precision)
+        c.seed, c.uid = int(d.seed), int(d.uid)
+    return arr
+
+
+class ModelHolder:
+    """C view of a model object (eps1, eps2, E0, nu, a, r_cut, rho_h and the
+    optional phi_tab/f_tab/F_tab arrays); keeps the arrays alive."""
+
+    def __init__(self, model):
+        m = ModelC()
+        m.eps1[:] = [float(x) for x in np.asarray(model.eps1, np.float64).ravel()]
+        m.eps2[:] = [float(x) for x in np.asarray(model.eps2, np.float64).ravel()]
+        m.E0[:] = [float(x) for x in model.E0]
+        m.nu, m.a, m.r_cut, m.rho_h = float(model.nu), float(model.a), float(model.r_cut), float(model.rho_h)
+        self.keep = []
+        if getattr(model, "phi_tab", None) is not None:
+            for name in ("phi_tab", "f_tab", "F_tab"):
+                arr = np.ascontiguousarray(getattr(model, name), dtype=np.float64)
+                self.keep.append(arr)
+                setattr(m, name, arr.ctypes.data)
+            m.n_r = int(model.phi_tab.shape[1])
+            m.n_rho = int(model.F_tab.shape[1])
+        self.c = m
+
+
+def workspace_bytes(descs, model, event_log_capacity=0) -> int:
+    lib = load_library()
+    cd = make_descs(descs)
+    mh = ModelHolder(model)
+    n = lib.akmc_workspace_bytes(ctypes.cast(cd, ctypes.c_void_p), len(descs), ctypes.byref(mh.c),
+                                 int(event_log_capacity))
+    if n == 0:
+        raise AkmcError(EINVAL, last_error())
+    return int(n)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Batch:
+    """A batch of independent voxels resident in one device workspace."""
+
+    def __init__(self, descs: Sequence, model, event_log_capacity: int = 0, device=None, stream=None,
+                 workspace=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("akmc needs a CUDA device; there is no CPU fallback")
+        self._lib = load_library()
+        self.descs = list(descs)
+        self.n = len(self.descs)
+        self.log_cap = int(event_log_capacity)
+        self._cdescs = make_descs(self.descs)
+        self._mh = ModelHolder(model)
+        self.nbytes = workspace_bytes(self.descs, model, self.log_cap)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if workspace is None:
+            workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        if workspace.numel() < self.nbytes:
+            raise AkmcError(ENOMEM, "workspace too small")
+        self.workspace = workspace
+        self.device = dev
+        h = ctypes.c_void_p()
+        _check(self._lib.akmc_create_batch(ctypes.cast(self._cdescs, ctypes.c_void_p), self.n,
+                                           ctypes.byref(self._mh.c), self.log_cap,
+                                           ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                           _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.akmc_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute_rates(self, stream=None):
+        _check(self._lib.akmc_compute_rates(self._h, _stream_ptr(stream)))
+
+    def step(self, n_events, stream=None):
+        """Run n_events (scalar or one per voxel) further events per voxel."""
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))
+        _check(self._lib.akmc_step_n(self._h, _ptr(arr), _stream_ptr(stream)))
+
+    def set_launch(self, warps: int, ctas_per_sm: int = 0):
+        _check(self._lib.akmc_set_launch(self._h, int(warps), int(ctas_per_sm)))
+
+    def read_state(self, voxel: int, species=True, log=False, stream=None):
+        d = self.descs[voxel]
+        nv, N = int(d.n_vac), 2 * int(d.L) ** 3
+        sp = np.empty(N, np.uint8) if species else None
+        pos = np.empty(nv, np.int32)
+        disp = np.empty(3 * nv, np.int32)
+        rates = np.empty(8 * nv, np.float64)
+        de = np.empty(8 * nv, np.float64)
+        lg = np.empty(self.log_cap, np.int32) if (log and self.log_cap) else None
+        st = StateC()
+        st.species, st.vac_pos, st.vac_disp = (sp.ctypes.data if sp is not None else None), pos.ctypes.data, \
+            disp.ctypes.data
+        st.rates, st.dE = rates.ctypes.data, de.ctypes.data
+        st.event_log = lg.ctypes.data if lg is not None else None
+        _check(self._lib.akmc_read_state(self._h, int(voxel), ctypes.byref(st), _stream_ptr(stream)))
+        return dict(species=sp, vac_pos=pos, vac_disp=disp.reshape(nv, 3), rates=rates.reshape(nv, 8),
+                    dE=de.reshape(nv, 8), t_hi=st.t_hi, t_lo=st.t_lo, n_events=int(st.n_events),
+                    status=int(st.status), event_log=lg)
+
+    def load_state(self, voxel, species, vac_pos, t_hi=0.0, t_lo=0.0, n_events=0, stream=None):
+        sp = np.ascontiguousarray(species, np.uint8)
+        vp = np.ascontiguousarray(vac_pos, np.int32)
+        _check(self._lib.akmc_load_state(self._h, int(voxel), _ptr(sp), _ptr(vp), float(t_hi), float(t_lo),
+                                         int(n_events), _stream_ptr(stream)))
+
+    def sync_status(self, stream=None):
+        per = np.zeros(self.n, np.int32)
+        st = self._lib.akmc_sync_status(self._h, _stream_ptr(stream), _ptr(per))
+        if st == ECUDA or st == EINVAL:
+            _check(st)
+        return int(st), per
+
+    def cluster_hist(self, voxel, mode=0, stream=None):
+        h = np.zeros(8, np.int64)
+        _check(self._lib.akmc_cluster_hist(self._h, int(voxel), int(mode), _ptr(h), _stream_ptr(stream)))
+        return h

@@ -1,0 +1,24 @@
+// akmc_launch.h -- host-side launchers of the libakmc kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include "akmc_device.cuh"
+
+namespace akmc {
+
+void launch_setup_model(ModelDev* M, int32_t* batch_status, int has_eam, int n_rho, cudaStream_t st);
+void launch_place(VoxelDev* vox, int n_vox, cudaStream_t st);
+
+// Density tiles: cells [x0,x0+kTX) x [y0,y0+kTY) x [z0,z0+kTZ) of one voxel.
+constexpr int kTX = 32, kTY = 16, kTZ = 16, kHalo = 2;
+cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab,
+                           const int4* items, int n_items, cudaStream_t st);
+
+size_t step_dyn_smem(int max_nv, int max_P);
+cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st);
+cudaError_t launch_rebuild(const BatchArgs& a, int warps, cudaStream_t st);
+int step_occupancy(int warps, int max_nv, int max_P);
+
+cudaError_t launch_cluster(const VoxelDev* vox, int voxel, int N, const Tables* tab, int mode,
+                           int32_t* labels, int32_t* sizes, unsigned long long* hist, cudaStream_t st);
+
+}  // namespace akmc

@@ -1,0 +1,88 @@
+// k_cluster.cu -- Cu cluster size histogram of one voxel (observable).
+// Clusters are connected components of Cu sites under 1nn+2nn (mode 0) or
+// 1nn (mode 1) adjacency.  Lock-free union-find over site labels: every
+// parent pointer points to a smaller site index, links go from the larger
+// root to the smaller one with compare-and-swap, so every loop below ends
+// after at most N iterations.  Scratch: labels[N], sizes[N] (int32).
+#include "akmc_device.cuh"
+#include "akmc_launch.h"
+
+namespace akmc {
+
+__device__ __forceinline__ int uf_find(int32_t* lab, int x) {
+    int p = lab[x];
+    while (p != x) {
+        int gp = lab[p];
+        if (gp != p) lab[x] = gp;   // path halving; gp is still an ancestor of x
+        x = p;
+        p = gp;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void uf_union(int32_t* lab, int a, int b) {
+    for (;;) {
+        a = uf_find(lab, a);
+        b = uf_find(lab, b);
+        if (a == b) return;
+        if (a > b) { int t = a; a = b; b = t; }
+        int old = atomicCAS(&lab[b], b, a);
+        if (old == b) return;
+        b = old;
+    }
+}
+
+__global__ void cluster_init(const uint8_t* sp, int N, int32_t* lab, int32_t* sizes) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        lab[i] = sp[i] == 1 ? i : -1;
+        sizes[i] = 0;
+    }
+}
+
+__global__ void cluster_hook(const uint8_t* sp, int L, int N, const Tables* tab, int n_adj, int32_t* lab) {
+    const int M2 = 2 * L;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        if (sp[i] != 1) continue;
+        const int b = i & 1, c = i >> 1;
+        const int X = 2 * (c % L) + b, Y = 2 * ((c / L) % L) + b, Z = 2 * (c / (L * L)) + b;
+        for (int k = 0; k < n_adj; ++k) {
+            const int o = tab->sph_off[k];
+            const int j = site_index(wrap_coord(X + off_dx(o), M2), wrap_coord(Y + off_dy(o), M2),
+                                     wrap_coord(Z + off_dz(o), M2), L);
+            if (j > i && sp[j] == 1) uf_union(lab, i, j);
+        }
+    }
+}
+
+__global__ void cluster_count(int N, int32_t* lab, int32_t* sizes) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        if (lab[i] < 0) continue;
+        atomicAdd(&sizes[uf_find(lab, i)], 1);
+    }
+}
+
+__global__ void cluster_bins(int N, const int32_t* lab, const int32_t* sizes, unsigned long long* hist) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        if (lab[i] != i) continue;
+        const int s = sizes[i];
+        const int bin = s <= 4 ? s - 1 : (s < 10 ? 4 : (s < 20 ? 5 : (s < 50 ? 6 : 7)));
+        atomicAdd(&hist[bin], 1ull);
+    }
+}
+
+cudaError_t launch_cluster(const VoxelDev* vox_host, int voxel, int N, const Tables* tab, int mode,
+                           int32_t* labels, int32_t* sizes, unsigned long long* hist, cudaStream_t st) {
+    const VoxelDev& V = vox_host[voxel];
+    const int threads = 256;
+    int blocks = (N + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    cudaError_t e = cudaMemsetAsync(hist, 0, 8 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    cluster_init<<<blocks, threads, 0, st>>>(V.species, N, labels, sizes);
+    cluster_hook<<<blocks, threads, 0, st>>>(V.species, V.L, N, tab, mode == 0 ? 14 : 8, labels);
+    cluster_count<<<blocks, threads, 0, st>>>(N, labels, sizes);
+    cluster_bins<<<blocks, threads, 0, st>>>(N, labels, sizes, hist);
+    return cudaGetLastError();
+}
+
+}  // namespace akmc

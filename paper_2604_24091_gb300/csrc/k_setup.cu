@@ -1,0 +1,174 @@
+// k_setup.cu -- model setup (shell constants, embedding coefficient tables)
+// and seeded species placement (step a1).
+#include "akmc_device.cuh"
+#include "akmc_launch.h"
+
+namespace akmc {
+
+// Cubic Hermite on a uniform grid, evaluated with explicitly rounded float64
+// operations in a fixed order (no fused multiply-add), so that shell
+// constants come out identical on every machine that evaluates the same form.
+__device__ double hermite_rn(const double* tab, int k, double t, double h) {
+    double v0 = tab[2 * k], d0 = __dmul_rn(tab[2 * k + 1], h);
+    double v1 = tab[2 * k + 2], d1 = __dmul_rn(tab[2 * k + 3], h);
+    double t2 = __dmul_rn(t, t), t3 = __dmul_rn(t2, t);
+    double h00 = __dadd_rn(__dsub_rn(__dmul_rn(2.0, t3), __dmul_rn(3.0, t2)), 1.0);
+    double h10 = __dadd_rn(__dsub_rn(t3, __dmul_rn(2.0, t2)), t);
+    double h01 = __dadd_rn(__dmul_rn(-2.0, t3), __dmul_rn(3.0, t2));
+    double h11 = __dsub_rn(t3, t2);
+    double s = __dadd_rn(__dmul_rn(h00, v0), __dmul_rn(h10, d0));
+    s = __dadd_rn(s, __dmul_rn(h01, v1));
+    return __dadd_rn(s, __dmul_rn(h11, d1));
+}
+
+__device__ double table_at_r(const double* tab, int n, double r_cut, double r) {
+    double dr = __ddiv_rn(r_cut, (double)(n - 1));
+    double x = __ddiv_rn(r, dr);
+    int k = (int)floor(x);
+    k = k > n - 2 ? n - 2 : (k < 0 ? 0 : k);
+    return hermite_rn(tab, k, __dsub_rn(x, (double)k), dr);
+}
+
+// Shell constants of the rigid bcc lattice: phi_ab and f_b at the 5 shell
+// radii r_s = (a/2) sqrt(3, 4, 8, 11, 12), f rounded to the 2^-24 density grid;
+// then the embedding tables: per interval the Hermite cubic in Horner form
+// F(t) = F_k + t (c1 + t (c2 + t c3)), t in [0,1), in FP64 and FP32, and the
+// knot values in 2^-40 eV fixed point.
+__global__ void setup_model_kernel(ModelDev* M, int32_t* batch_status) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    if (M->has_eam) {
+        const int len2[6] = {0, 3, 4, 8, 11, 12};
+        if (blockIdx.x == 0) {
+            for (int i = threadIdx.x; i < 10 * 8; i += blockDim.x) {
+                M->phi_d[i / 8][i % 8] = 0.0;
+                M->phi_q[i / 8][i % 8] = 0;
+            }
+            for (int i = threadIdx.x; i < 5 * 8; i += blockDim.x) M->fq[i / 8][i % 8] = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < 14 * 5; i += blockDim.x) {
+                int fn = i / 5, s = i % 5 + 1;
+                double r = __dmul_rn(__dmul_rn(M->a, 0.5), __dsqrt_rn((double)len2[s]));
+                if (fn < 10) {
+                    double v = table_at_r(M->phi_tab + (size_t)fn * M->n_r * 2, M->n_r, M->r_cut, r);
+                    M->phi_d[fn][s] = v;
+                    M->phi_q[fn][s] = llround(v * 0x1p40);
+                } else {
+                    int b = fn - 10;
+                    double v = table_at_r(M->f_tab + (size_t)b * M->n_r * 2, M->n_r, M->r_cut, r);
+                    long long q = llround(v * 0x1p24);
+                    if (q < 0 || q > (1 << 26)) atomicExch(batch_status, kEINVAL);
+                    M->fq[b][s] = (int32_t)q;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < 5 * 8) {
+                int b = threadIdx.x / 8, s = threadIdx.x % 8;
+                M->cq[b][s] = M->fq[b][s] - M->fq[kFe][s];
+            }
+            if (threadIdx.x == 0) {
+                const int cnt[6] = {0, 8, 6, 12, 24, 8};
+                long long pure = 0, mx = 0;
+                for (int s = 1; s <= 5; ++s) {
+                    pure += (long long)cnt[s] * M->fq[kFe][s];
+                    int best = 0;
+                    for (int b = 0; b < 4; ++b) best = max(best, M->fq[b][s]);
+                    mx += (long long)cnt[s] * best;
+                }
+                if (mx >= (1LL << 30)) atomicExch(batch_status, kEINVAL);
+                M->rho_pure = (int32_t)pure;
+                M->rho_max = (int32_t)min(mx, (long long)(1 << 30));
+            }
+        }
+        const int nint = M->n_rho - 1;
+        const double h = M->rho_h;
+        for (int i = tid; i < 4 * M->n_rho; i += nth) {
+            int a = i / M->n_rho, k = i % M->n_rho;
+            const double* T = M->F_tab + (size_t)a * M->n_rho * 2;
+            double F0 = T[2 * k];
+            M->Fq[i] = llround(F0 * 0x1p40);
+            if (k < nint) {
+                double d0 = T[2 * k + 1] * h, F1 = T[2 * k + 2], d1 = T[2 * k + 3] * h;
+                double c1 = d0;
+                double c2 = 3.0 * (F1 - F0) - (2.0 * d0 + d1);
+                double c3 = 2.0 * (F0 - F1) + (d0 + d1);
+                M->Fd[(size_t)a * nint + k] = Cubic64{F0, c1, c2, c3};
+                M->Ff[(size_t)a * nint + k] = make_float4((float)c1, (float)c2, (float)c3, 0.f);
+            }
+        }
+    }
+}
+
+// (a1) Placement: species counts n_s = floor(frac_s N + 0.5); draw k of the
+// placement stream gives site floor(r * N / 2^64) from 64 Philox bits; the
+// draw is taken if the site still holds Fe.  Order: vacancies (slot = order
+// of placement), Cu, Ni, Mn.  One warp per voxel evaluates 32 consecutive
+// draws at once and resolves them in draw order (a draw is taken iff its site
+// is Fe and no earlier draw of the same batch hit that site).
+__global__ void place_kernel(VoxelDev* vox, int n_vox) {
+    const int lane = threadIdx.x & 31;
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (v >= n_vox) return;
+    VoxelDev& V = vox[v];
+    const int N = V.N;
+    int cnt[4];
+    cnt[0] = V.nv;
+    long long total = V.nv;
+    for (int s = 0; s < 3; ++s) {
+        cnt[s + 1] = (int)floor(V.frac[s] * (double)N + 0.5);
+        total += cnt[s + 1];
+    }
+    if (lane == 0) for (int s = 0; s < 4; ++s) V.counts[s] = cnt[s];
+    const uint32_t k0 = (uint32_t)V.seed, k1 = (uint32_t)(V.seed >> 32);
+    const uint32_t w2 = (uint32_t)V.uid, w3 = 0x80000000u | (uint32_t)(V.uid >> 32);
+    const uint64_t max_draws = 64ull * (uint64_t)N + 65536ull;
+    uint8_t* sp = V.species;
+    long long placed = 0;
+    uint64_t kb = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    while (placed < total) {
+        if (kb > max_draws) {
+            if (lane == 0) V.status = kEINVAL;
+            return;
+        }
+        uint64_t k = kb + lane;
+        uint32_t c0 = (uint32_t)k, c1 = (uint32_t)(k >> 32), c2 = w2, c3 = w3;
+        philox4x32_10(c0, c1, c2, c3, k0, k1);
+        uint64_t r = ((uint64_t)c0 << 32) | c1;
+        int site = (int)__umul64hi(r, (uint64_t)N);
+        int cur = sp[site];
+        unsigned peers = __match_any_sync(0xffffffffu, site);
+        bool first = (peers & lt_mask) == 0;
+        bool take = first && cur == kFe;
+        unsigned acc = __ballot_sync(0xffffffffu, take);
+        int rank = __popc(acc & lt_mask);
+        long long q = placed + rank;
+        if (take && q < total) {
+            int species;
+            long long qq = q;
+            if (qq < cnt[0]) species = kVac;
+            else if ((qq -= cnt[0]) < cnt[1]) species = 1;
+            else if ((qq -= cnt[1]) < cnt[2]) species = 2;
+            else species = 3;
+            sp[site] = (uint8_t)species;
+            if (species == kVac) V.vac_pos[q] = site;
+        }
+        placed += __popc(acc);
+        kb += 32;
+        __syncwarp();
+    }
+}
+
+void launch_setup_model(ModelDev* M, int32_t* batch_status, int has_eam, int n_rho, cudaStream_t st) {
+    int blocks = has_eam ? (4 * n_rho + 255) / 256 : 1;
+    if (blocks < 1) blocks = 1;
+    setup_model_kernel<<<blocks, 256, 0, st>>>(M, batch_status);
+}
+
+void launch_place(VoxelDev* vox, int n_vox, cudaStream_t st) {
+    int threads = 128;
+    int blocks = (n_vox * 32 + threads - 1) / threads;
+    place_kernel<<<blocks, threads, 0, st>>>(vox, n_vox);
+}
+
+}  // namespace akmc

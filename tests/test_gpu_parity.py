@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle on the same
+seeded inputs.
+
+Bars: integer/index results (placement, lattice occupancy, event indices,
+displacements, cluster histograms) bit-exact; float64 rates within 1e-12
+relative; the clock within 1e-12 relative; FP32/FP64 split EAM energy changes
+within 1e-5 eV of the oracle's float64 values on the same state.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2604_24091_gb300 import Batch, ETRAPPED, ENUMERIC  # noqa: E402
+
+RATE_RTOL = 1e-12
+SPLIT_DE_TOL = 1e-5
+
+
+def _assert_rates(g, o, rtol=RATE_RTOL):
+    g, o = np.asarray(g), np.asarray(o)
+    assert np.array_equal(g == 0, o == 0)
+    np.testing.assert_allclose(g, o, rtol=rtol, atol=0)
+
+
+def _time(s):
+    return s["t_hi"] + s["t_lo"]
+
+
+def _mixed_descs():
+    P, E = synth.PAIR_MODEL, synth.EAM_MODEL
+    F, S = synth.PREC_FP64, synth.PREC_SPLIT
+    return [synth.VoxelDesc(3, 1, (0.05, 0.0, 0.0), 563.0, P, F, seed=1, uid=10),
+            synth.VoxelDesc(5, 4, (0.10, 0.08, 0.06), 543.0, P, F, seed=2, uid=11),
+            synth.VoxelDesc(16, 1, (0.0134, 0.0, 0.0), 563.0, P, F, seed=3, uid=12),
+            synth.VoxelDesc(4, 2, (0.10, 0.10, 0.10), 593.0, E, F, seed=4, uid=13),
+            synth.VoxelDesc(7, 3, (0.08, 0.05, 0.05), 563.0, E, S, seed=5, uid=14),
+            synth.VoxelDesc(9, 5, (0.06, 0.06, 0.06), 570.0, E, F, seed=6, uid=15),
+            synth.VoxelDesc(33, 2, (0.003, 0.007, 0.014), 563.0, E, S, seed=7, uid=16)]
+
+
+def test_placement_and_initial_rates(model):
+    descs = _mixed_descs()
+    b = Batch(descs, model)
+    for v, d in enumerate(descs):
+        g = b.read_state(v)
+        o = oracle.Voxel(d, model).state()
+        assert np.array_equal(g["species"], o["species"]), v
+        assert np.array_equal(g["vac_pos"], o["vac_pos"]), v
+        if d.model == synth.PAIR_MODEL:
+            assert np.array_equal(g["dE"], o["dE"])
+            _assert_rates(g["rates"], o["rates"])
+        elif d.precision == synth.PREC_FP64:
+            np.testing.assert_allclose(g["dE"], o["dE"], rtol=0, atol=1e-12)
+            _assert_rates(g["rates"], o["rates"])
+        else:
+            assert np.abs(g["dE"] - o["dE"]).max() <= SPLIT_DE_TOL
+            _assert_rates(g["rates"], o["rates"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+def test_pair_trajectory_bit_exact(model, warps):
+    # plain configuration (16^3 cells, Fe-1.34Cu, 1 vacancy) and a dense
+    # multi-vacancy lattice, stepped in two chunks
+    descs = [synth.config_plain_pair()[0],
+             synth.VoxelDesc(8, 6, (0.12, 0.1, 0.08), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=9, uid=3)]
+    n1, n2 = 20000, 30000
+    b = Batch(descs, model, event_log_capacity=n1 + n2)
+    b.set_launch(warps, 0)
+    b.step(n1)
+    b.step(n2)
+    assert b.sync_status()[0] == 0
+    for v, d in enumerate(descs):
+        o = oracle.Voxel(d, model)
+        log_o = o.step(n1 + n2, log=True)
+        g = b.read_state(v, log=True)
+        so = o.state()
+        first_bad = np.flatnonzero(g["event_log"] != log_o)
+        assert first_bad.size == 0, "voxel %d diverges at event %d" % (v, first_bad[0])
+        assert np.array_equal(g["species"], so["species"])
+        assert np.array_equal(g["vac_pos"], so["vac_pos"])
+        assert np.array_equal(g["vac_disp"], so["vac_disp"])
+        assert g["n_events"] == so["n_events"] == n1 + n2
+        assert abs(_time(g) - _time(so)) <= 1e-12 * _time(so)
+        _assert_rates(g["rates"], so["rates"])
+
+
+def test_eam_fp64_trajectory(model):
+    descs = [synth.VoxelDesc(6, 3, (0.10, 0.08, 0.08), 563.0, synth.EAM_MODEL, synth.PREC_FP64, seed=21, uid=5),
+             synth.VoxelDesc(4, 2, (0.12, 0.12, 0.12), 593.0, synth.EAM_MODEL, synth.PREC_FP64, seed=22, uid=6)]
+    n = 3000
+    b = Batch(descs, model, event_log_capacity=n)
+    b.step(n)
+    assert b.sync_status()[0] == 0
+    for v, d in enumerate(descs):
+        o = oracle.Voxel(d, model)
+        log_o = o.step(n, log=True)
+        g = b.read_state(v, log=True)
+        so = o.state()
+        assert np.array_equal(g["event_log"], log_o)
+        assert np.array_equal(g["species"], so["species"])
+        np.testing.assert_allclose(g["dE"], so["dE"], rtol=0, atol=1e-12)
+        _assert_rates(g["rates"], so["rates"])
+        assert abs(_time(g) - _time(so)) <= 1e-12 * _time(so)
+
+
+def test_eam_split_energy_error(model):
+    # FP32 embedding / exact fixed-point assembly: every hop's dE within 1e-5 eV
+    # of the float64 oracle on the GPU's own state, after many events.
+    descs = [synth.VoxelDesc(8, 4, (0.08, 0.08, 0.08), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT, seed=31, uid=7),
+             synth.VoxelDesc(32, 1, (0.003, 0.007, 0.014), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT,
+                             seed=32, uid=8)]
+    b = Batch(descs, model)
+    worst = 0.0
+    for _ in range(3):
+        b.step(1500)
+        assert b.sync_status()[0] == 0
+        for v, d in enumerate(descs):
+            g = b.read_state(v)
+            o = oracle.Voxel(d, model)
+            o.load(g["species"], g["vac_pos"])
+            so = o.state()
+            worst = max(worst, float(np.abs(g["dE"] - so["dE"]).max()))
+            _assert_rates(g["rates"], so["rates"], rtol=1e-3)
+            assert np.array_equal(np.bincount(g["species"], minlength=5),
+                                  np.bincount(oracle.Voxel(d, model).state()["species"], minlength=5))
+    assert worst <= SPLIT_DE_TOL, worst
+
+
+def test_batch_and_launch_shape_invariance(model):
+    descs = _mixed_descs()
+    n = 800
+    alone = []
+    for v, d in enumerate(descs):
+        b = Batch([d], model, event_log_capacity=n)
+        b.step(n)
+        alone.append(b.read_state(0, log=True))
+        b.close()
+    for warps in (1, 8):
+        b = Batch(descs, model, event_log_capacity=n)
+        b.set_launch(warps, 1)
+        b.step(n)
+        for v in range(len(descs)):
+            g = b.read_state(v, log=True)
+            assert np.array_equal(g["event_log"], alone[v]["event_log"])
+            assert np.array_equal(g["species"], alone[v]["species"])
+            assert np.array_equal(g["rates"], alone[v]["rates"])
+            assert g["t_hi"] == alone[v]["t_hi"] and g["t_lo"] == alone[v]["t_lo"]
+
+
+def test_uneven_targets_and_resume(model):
+    descs = _mixed_descs()
+    targets = np.array([0, 500, 1200, 300, 0, 700, 250], np.uint64)
+    b = Batch(descs, model, event_log_capacity=4000)
+    b.step(targets)
+    states = [b.read_state(v) for v in range(len(descs))]
+    for v, d in enumerate(descs):
+        assert states[v]["n_events"] == int(targets[v])
+    # resume voxel 2 into a fresh batch from its state and continue
+    d = descs[2]
+    s = states[2]
+    c = Batch([d], model, event_log_capacity=4000)
+    c.load_state(0, s["species"], s["vac_pos"], s["t_hi"], s["t_lo"], s["n_events"])
+    c.step(900)
+    b.step(np.array([0, 0, 900, 0, 0, 0, 0], np.uint64))
+    g1, g2 = b.read_state(2, log=True), c.read_state(0, log=True)
+    assert np.array_equal(g1["species"], g2["species"])
+    assert g1["t_hi"] == g2["t_hi"] and g1["t_lo"] == g2["t_lo"]
+    idx = np.arange(1200, 2100) % 4000
+    assert np.array_equal(g1["event_log"][idx], g2["event_log"][idx])
+    o = oracle.Voxel(d, model)
+    log_o = o.step(2100, log=True)
+    assert np.array_equal(g1["event_log"][np.arange(2100)], log_o)
+
+
+def test_trapped_and_numeric_status(model):
+    L = 3
+    d = synth.VoxelDesc(L, 1, (0.0, 0.0, 0.0), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=1, uid=1)
+    dd = synth.VoxelDesc(L, 2 * L ** 3, (0.0, 0.0, 0.0), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=1, uid=2)
+    if dd.n_vac <= 256:
+        b = Batch([d, dd], model)
+        b.step(10)
+        st, per = b.sync_status()
+        assert per[1] == ETRAPPED and per[0] == 0 and st == ETRAPPED
+        assert b.read_state(1)["n_events"] == 0
+    import copy
+    m = copy.deepcopy(model)
+    m.F_tab = m.F_tab[:, :200, :].copy()
+    e = synth.VoxelDesc(4, 1, (0.0, 0.0, 0.0), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT, seed=2, uid=2)
+    b = Batch([e], m)
+    st, per = b.sync_status()
+    assert per[0] == ENUMERIC
+    assert oracle.Voxel(e, m).status == oracle.ENUMERIC
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cluster_histogram_matches_oracle(model, mode):
+    descs = [synth.VoxelDesc(10, 2, (0.10, 0.02, 0.02), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=41, uid=1),
+             synth.VoxelDesc(16, 1, (0.03, 0.0, 0.0), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=42, uid=2),
+             synth.VoxelDesc(12, 3, (0.2, 0.0, 0.0), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT, seed=43, uid=3)]
+    b = Batch(descs, model)
+    b.step(2000)
+    for v, d in enumerate(descs):
+        g = b.read_state(v)
+        o = oracle.Voxel(d, model)
+        o.load(g["species"], g["vac_pos"])
+        assert b.cluster_hist(v, mode).tolist() == o.cluster_hist(mode)[0].tolist()
+
+
+def test_full_size_batched_eam_sampled(model):
+    # The benchmark workload (256 voxels of 32^3 cells, EAM split) in the
+    # benchmark's launch configuration: sampled voxels checked against the oracle.
+    descs = synth.config_batched_eam(256)
+    b = Batch(descs, model)
+    b.step(2000)
+    st, per = b.sync_status()
+    assert st == 0
+    for v in (0, 77, 255):
+        g = b.read_state(v)
+        assert g["n_events"] == 2000
+        o = oracle.Voxel(descs[v], model)
+        init = o.state()["species"]
+        assert np.array_equal(np.bincount(g["species"], minlength=5), np.bincount(init, minlength=5))
+        o.load(g["species"], g["vac_pos"])
+        assert np.abs(g["dE"] - o.state()["dE"]).max() <= SPLIT_DE_TOL
+        _assert_rates(g["rates"], o.state()["rates"], rtol=1e-3)
+        assert _time(g) > 0
