@@ -150,6 +150,26 @@ akmc_status akmc_load_state(akmc_batch* batch, int32_t voxel, const uint8_t* spe
                             const int32_t* vac_pos, double t_hi, double t_lo,
                             uint64_t n_events, akmc_stream stream);
 
+/* Whole-batch state transfer, for checkpointing and host-fed pipelines.
+ * Arrays are concatenated in voxel order: species (sum of 2L^3 bytes),
+ * vac_pos and (read only) vac_disp (sum of n_vac, 3 n_vac int32); the
+ * per-voxel arrays have n_voxels entries.  Pass pinned host memory for
+ * copies that overlap; both calls are stream-ordered and do not synchronise
+ * (the host buffers must stay valid until the stream reaches the copies).
+ * load_batch_state does no host-side validation of the lattices: each
+ * voxel's vac_pos must name its vacancy sites (the next rebuild flags
+ * violations).  NULL t_hi/t_lo/n_events leave the clock and counters as they
+ * are.  The next akmc_step_n or akmc_compute_rates rebuilds rates first. */
+akmc_status akmc_load_batch_state(akmc_batch* batch, const uint8_t* species, const int32_t* vac_pos,
+                                  const double* t_hi, const double* t_lo, const uint64_t* n_events,
+                                  akmc_stream stream);
+akmc_status akmc_read_batch_state(akmc_batch* batch, uint8_t* species, int32_t* vac_pos, int32_t* vac_disp,
+                                  double* t_hi, double* t_lo, uint64_t* n_events, int32_t* status,
+                                  akmc_stream stream);
+/* Bytes of the concatenated species array, and number of vacancy slots. */
+size_t akmc_batch_sites(const akmc_batch* batch);
+int64_t akmc_batch_vacancies(const akmc_batch* batch);
+
 /* Synchronise the stream and report voxel statuses: per_voxel (nullable,
  * n_voxels entries); returns AKMC_OK if every voxel is OK, else the status
  * of the lowest-indexed voxel that is not. */

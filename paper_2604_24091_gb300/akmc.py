@@ -68,6 +68,10 @@ def load_library():
             "akmc_read_state": (I32, [P, I32, ctypes.POINTER(StateC), P]),
             "akmc_load_state": (I32, [P, I32, P, P, ctypes.c_double, ctypes.c_double, U64, P]),
             "akmc_sync_status": (I32, [P, P, P]),
+            "akmc_load_batch_state": (I32, [P, P, P, P, P, P, P]),
+            "akmc_read_batch_state": (I32, [P, P, P, P, P, P, P, P, P]),
+            "akmc_batch_sites": (SZ, [P]),
+            "akmc_batch_vacancies": (ctypes.c_int64, [P]),
             "akmc_cluster_hist": (I32, [P, I32, I32, P, P]),
             "akmc_set_launch": (I32, [P, I32, I32]),
             "akmc_n_voxels": (I32, [P]),
@@ -221,10 +225,58 @@ class Batch:
         _check(self._lib.akmc_load_state(self._h, int(voxel), _ptr(sp), _ptr(vp), float(t_hi), float(t_lo),
                                          int(n_events), _stream_ptr(stream)))
 
+    @property
+    def n_sites_total(self) -> int:
+        return int(self._lib.akmc_batch_sites(self._h))
+
+    @property
+    def n_vac_total(self) -> int:
+        return int(self._lib.akmc_batch_vacancies(self._h))
+
+    def load_batch_state(self, species, vac_pos, t_hi=None, t_lo=None, n_events=None, stream=None):
+        """Stream-ordered whole-batch load from host arrays (concatenated in
+        voxel order); numpy arrays must stay alive until the stream passes."""
+        def p(a, dt):
+            if a is None:
+                return None
+            assert a.dtype == dt and a.flags.c_contiguous
+            return ctypes.c_void_p(a.ctypes.data)
+        _check(self._lib.akmc_load_batch_state(self._h, p(species, np.uint8), p(vac_pos, np.int32),
+                                               p(t_hi, np.float64), p(t_lo, np.float64),
+                                               p(n_events, np.uint64), _stream_ptr(stream)))
+
+    def read_batch_state(self, out, stream=None):
+        """Stream-ordered whole-batch read into the host arrays of `out`
+        (keys species, vac_pos, vac_disp, t_hi, t_lo, n_events, status)."""
+        def p(k):
+            a = out.get(k)
+            return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+        _check(self._lib.akmc_read_batch_state(self._h, p("species"), p("vac_pos"), p("vac_disp"), p("t_hi"),
+                                               p("t_lo"), p("n_events"), p("status"), _stream_ptr(stream)))
+
+    def host_buffers(self, pinned=True):
+        """Host arrays sized for read/load_batch_state (pinned through torch)."""
+        import torch
+
+        def arr(n, dt):
+            t = torch.empty(int(n), dtype=dt, pin_memory=pinned)
+            return t.numpy(), t
+        keep = []
+        out = {}
+        for k, n, dt in (("species", self.n_sites_total, torch.uint8), ("vac_pos", self.n_vac_total, torch.int32),
+                         ("vac_disp", 3 * self.n_vac_total, torch.int32), ("t_hi", self.n, torch.float64),
+                         ("t_lo", self.n, torch.float64), ("n_events", self.n, torch.int64),
+                         ("status", self.n, torch.int32)):
+            a, t = arr(n, dt)
+            keep.append(t)
+            out[k] = a.view(np.uint64) if k == "n_events" else a
+        out["_keep"] = keep
+        return out
+
     def sync_status(self, stream=None):
         per = np.zeros(self.n, np.int32)
         st = self._lib.akmc_sync_status(self._h, _stream_ptr(stream), _ptr(per))
-        if st == ECUDA or st == EINVAL:
+        if st == ECUDA:
             _check(st)
         return int(st), per
 

@@ -42,6 +42,12 @@ struct Tables {
     int32_t eam_mk[8];
     uint32_t eam_ent[8][80];   // idx | s_ip<<8 | s_im<<11 | own<<14   (shell 0 = outside)
     int32_t sph_off[64];       // the 58 cutoff-sphere offsets, extra = shell
+    // For the EAM union stencil around a vacancy that has just moved from w
+    // to m = w + d_k (entry u at offset o_u from m): (shell(u - w) << 3) |
+    // shell(u - m), the shells of the density change f_A(r_uw) - f_A(r_um)
+    // that the hop caused at u.  [0]: L >= 5; [1]: L = 4 (u - w taken as the
+    // periodic minimal image).
+    uint8_t eam_dsh[2][160][8];
 };
 
 struct ModelDev {
@@ -50,6 +56,9 @@ struct ModelDev {
     double nu;
     double a, r_cut, rho_h, inv_knot;   // inv_knot = 2^-shift
     int32_t n_r, n_rho, shift, has_eam;
+    int32_t thr_hi[4];         // dE_q > thr_hi[A]  <=>  dE > 2 E0[A]   (dE_q in units of 2^-24 eV)
+    int32_t thr_lo[4];         // dE_q < thr_lo[A]  <=>  dE < -2 E0[A]
+    double two_E0[4];
     int32_t rho_pure;          // perfect-Fe density (fixed point)
     int32_t rho_max;           // largest density any site can reach (fixed point)
     int32_t fq[5][8];          // density contribution f_b(shell), row V = 0, shell 0 = 0
@@ -83,7 +92,15 @@ struct VoxelDev {
     double* tree;              // [2P], node 1 = root
     uint8_t* hop_sp;           // [8 nv] species at each hop target
     int32_t* log;              // [log_cap]
+    double* etab;              // [kEtab] rate tables of this temperature (see kEtab)
+    int32_t etab_ok;           // tables finite and nonzero (else rates use exp directly)
+    int32_t pad_;
 };
+
+// Per-voxel rate tables: exp(-beta * i * 2^(9k) * 2^-25) for k = 0,1,2 and
+// i < 512 (energies on the 2^-25 eV grid below 4 eV), then for each jumping
+// species A the constant nu * exp(beta * (2 - E0[A])).
+constexpr int kEtab = 3 * 512 + 4;
 
 struct BatchArgs {
     VoxelDev* vox;

@@ -133,6 +133,18 @@ Tables make_tables() {
         T.eam_ent[k][e++] = 1u << 14;   // the moving atom's own embedding term
     }
     for (size_t i = 0; i < E.size(); ++i) T.eam_off[i] = off_pack(E[i].dx, E[i].dy, E[i].dz, 0);
+    for (int small = 0; small < 2; ++small)
+        for (size_t u = 0; u < E.size(); ++u)
+            for (int k = 0; k < 8; ++k) {
+                Off3 uw = plus(E[u], dirs[k]);   // u - w with w = m - d_k
+                if (small) {
+                    auto img = [](int c) { return c > 4 ? c - 8 : (c <= -4 ? c + 8 : c); };
+                    uw = Off3{img(uw.dx), img(uw.dy), img(uw.dz)};
+                }
+                int sw = contains(sph, uw) ? shell_of(uw) : 0;
+                int sm = contains(sph, E[u]) ? shell_of(E[u]) : 0;
+                T.eam_dsh[small][u][k] = (uint8_t)((sw << 3) | sm);
+            }
     return T;
 }
 
@@ -201,6 +213,8 @@ akmc_status validate(const akmc_voxel_desc* descs, int32_t n, const akmc_model* 
         }
     if (!all_finite(m->E0, 4) || !(m->nu > 0.0) || !std::isfinite(m->nu))
         return fail(AKMC_EINVAL, "bad E0 or nu");
+    for (int a = 0; a < 4; ++a)
+        if (!(m->E0[a] >= 0.0 && m->E0[a] < 4.0)) return fail(AKMC_EINVAL, "E0 must lie in [0, 4) eV");
     if (*has_eam) {
         if (m->n_r < 2 || m->n_rho < 2 || !m->phi_tab || !m->f_tab || !m->F_tab)
             return fail(AKMC_EINVAL, "EAM voxels need phi/f/F tables");
@@ -228,8 +242,9 @@ struct Layout {
     size_t status = 0, model = 0, tab = 0, vox = 0, targets = 0, order = 0, queue = 0, hist = 0;
     size_t phi_raw = 0, f_raw = 0, F_raw = 0, Fd = 0, Ff = 0, Fq = 0, items = 0;
     size_t labels = 0, sizes = 0, total = 0;
-    std::vector<size_t> species, rho, pos, disp, rates, dE, hop, tree, log;
-    size_t state_begin = 0, state_end = 0;
+    std::vector<size_t> species, rho, pos, disp, rates, dE, hop, tree, log, etab;
+    size_t state_begin = 0, state_end = 0, io = 0;
+    size_t b_species = 0, b_pos = 0, b_disp = 0, tot_N = 0, tot_nv = 0;
     std::vector<int4> item_list;
     int max_nv = 1, max_P = 1;
     size_t max_N = 0;
@@ -265,22 +280,49 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         }
         Lo.items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
     }
+    Lo.io = take(32 * (size_t)n);
+    // Per-voxel state, each kind concatenated in voxel order so that whole-batch
+    // transfers are single copies.
     Lo.state_begin = o;
+    size_t tot_N = 0, tot_rho = 0, tot_nv = 0, tot_P = 0;
     for (int32_t v = 0; v < n; ++v) {
         size_t N = 2 * (size_t)d[v].L * d[v].L * d[v].L;
         int nv = d[v].n_vac, P = next_pow2(nv);
         Lo.max_nv = std::max(Lo.max_nv, nv);
         Lo.max_P = std::max(Lo.max_P, P);
         Lo.max_N = std::max(Lo.max_N, N);
-        Lo.species.push_back(take(N));
-        Lo.rho.push_back(d[v].model == AKMC_EAM ? take(sizeof(int32_t) * N) : 0);
-        Lo.pos.push_back(take(sizeof(int32_t) * nv));
-        Lo.disp.push_back(take(sizeof(int32_t) * 3 * nv));
-        Lo.rates.push_back(take(sizeof(double) * 8 * nv));
-        Lo.dE.push_back(take(sizeof(double) * 8 * nv));
-        Lo.hop.push_back(take(8 * (size_t)nv));
-        Lo.tree.push_back(take(sizeof(double) * 2 * P));
-        Lo.log.push_back(log_cap > 0 ? take(sizeof(int32_t) * log_cap) : 0);
+        Lo.species.push_back(tot_N);
+        Lo.rho.push_back(d[v].model == AKMC_EAM ? tot_rho : 0);
+        Lo.pos.push_back(tot_nv);
+        Lo.tree.push_back(tot_P);
+        tot_N += N;
+        if (d[v].model == AKMC_EAM) tot_rho += N;
+        tot_nv += nv;
+        tot_P += 2 * (size_t)P;
+    }
+    Lo.tot_N = tot_N;
+    Lo.tot_nv = tot_nv;
+    const size_t b_species = take(tot_N), b_rho = take(sizeof(int32_t) * tot_rho);
+    const size_t b_pos = take(sizeof(int32_t) * tot_nv), b_disp = take(sizeof(int32_t) * 3 * tot_nv);
+    const size_t b_rates = take(sizeof(double) * 8 * tot_nv), b_dE = take(sizeof(double) * 8 * tot_nv);
+    const size_t b_hop = take(8 * tot_nv), b_tree = take(sizeof(double) * tot_P);
+    const size_t b_log = take(sizeof(int32_t) * (size_t)log_cap * n);
+    const size_t b_etab = take(sizeof(double) * kEtab * (size_t)n);
+    Lo.b_species = b_species;
+    Lo.b_pos = b_pos;
+    Lo.b_disp = b_disp;
+    for (int32_t v = 0; v < n; ++v) {
+        const size_t nv0 = Lo.pos[v];
+        Lo.species[v] += b_species;
+        Lo.rho[v] = d[v].model == AKMC_EAM ? b_rho + sizeof(int32_t) * Lo.rho[v] : 0;
+        Lo.pos[v] = b_pos + sizeof(int32_t) * nv0;
+        Lo.disp.push_back(b_disp + sizeof(int32_t) * 3 * nv0);
+        Lo.rates.push_back(b_rates + sizeof(double) * 8 * nv0);
+        Lo.dE.push_back(b_dE + sizeof(double) * 8 * nv0);
+        Lo.hop.push_back(b_hop + 8 * nv0);
+        Lo.tree[v] = b_tree + sizeof(double) * Lo.tree[v];
+        Lo.log.push_back(log_cap > 0 ? b_log + sizeof(int32_t) * (size_t)log_cap * v : 0);
+        Lo.etab.push_back(b_etab + sizeof(double) * kEtab * (size_t)v);
     }
     Lo.state_end = o;
     Lo.labels = take(sizeof(int32_t) * Lo.max_N);
@@ -300,11 +342,14 @@ struct akmc_batch {
     std::vector<VoxelDev> vox_host;    // pointers and constants (device copy is authoritative for state)
     ModelDev model_host{};
     std::vector<double> phi_raw, f_raw, F_raw;
-    char* staging = nullptr;           // pinned: targets + order
-    cudaEvent_t staging_done = nullptr;
-    bool staging_used = false;
+    static constexpr int kStage = 4;   // ring of pinned staging slots: targets + order
+    char* staging = nullptr;
+    cudaEvent_t staging_done[kStage] = {};
+    bool staging_used[kStage] = {};
+    int stage = 0;
     bool dirty = false;
     int warps = 4, ctas_per_sm = 0, n_sm = 0, device = 0;
+    int occupancy[9] = {};             // CTAs per SM of the step kernel, by warps per CTA
 
     BatchArgs args() const {
         BatchArgs a;
@@ -379,7 +424,12 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
         M.eps_q[0][i] = (int32_t)(m->eps1[i] * 16777216.0);
         M.eps_q[1][i] = (int32_t)(m->eps2[i] * 16777216.0);
     }
-    for (int i = 0; i < 4; ++i) M.E0[i] = m->E0[i];
+    for (int i = 0; i < 4; ++i) {
+        M.E0[i] = m->E0[i];
+        M.two_E0[i] = 2.0 * m->E0[i];
+        M.thr_hi[i] = (int32_t)std::floor(2.0 * m->E0[i] * 16777216.0);
+        M.thr_lo[i] = -M.thr_hi[i];
+    }
     M.nu = m->nu;
     M.has_eam = has_eam;
     if (has_eam) {
@@ -429,9 +479,12 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
         V.hop_sp = (uint8_t*)(b->base + lo.hop[v]);
         V.tree = (double*)(b->base + lo.tree[v]);
         V.log = log_cap > 0 ? (int32_t*)(b->base + lo.log[v]) : nullptr;
+        V.etab = (double*)(b->base + lo.etab[v]);
     }
-    cudaError_t e = cudaMallocHost((void**)&b->staging, (sizeof(uint64_t) + sizeof(int32_t)) * n);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staging_done, cudaEventDisableTiming);
+    const size_t stage_bytes = (sizeof(uint64_t) + sizeof(int32_t)) * n;
+    cudaError_t e = cudaMallocHost((void**)&b->staging, stage_bytes * akmc_batch::kStage);
+    for (int i = 0; i < akmc_batch::kStage && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&b->staging_done[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         akmc_destroy_batch(b);
         return fail(AKMC_ECUDA, "pinned staging: %s", cudaGetErrorString(e));
@@ -454,8 +507,9 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
                              cudaMemcpyHostToDevice, s));
     AKMC_TRY(cudaMemcpyAsync(b->base + lo.targets, b->staging, (sizeof(uint64_t) + sizeof(int32_t)) * n,
                              cudaMemcpyHostToDevice, s));
-    AKMC_TRY(cudaEventRecord(b->staging_done, s));
-    b->staging_used = true;
+    AKMC_TRY(cudaEventRecord(b->staging_done[0], s));
+    b->staging_used[0] = true;
+    b->stage = 1;
     if (has_eam) {
         AKMC_TRY(cudaMemcpyAsync(b->base + lo.phi_raw, b->phi_raw.data(), sizeof(double) * b->phi_raw.size(),
                                  cudaMemcpyHostToDevice, s));
@@ -473,6 +527,7 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
     AKMC_TRY(cudaGetLastError());
     launch_place((VoxelDev*)(b->base + lo.vox), n, s);
     AKMC_TRY(cudaGetLastError());
+    AKMC_TRY(launch_rate_tables((VoxelDev*)(b->base + lo.vox), n, (const ModelDev*)(b->base + lo.model), s));
     // The pageable host images above must outlive their copies.
     AKMC_TRY(cudaStreamSynchronize(s));
 #undef AKMC_TRY
@@ -497,9 +552,12 @@ akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream str
         akmc_status st = rebuild(b, s);
         if (st != AKMC_OK) return st;
     }
-    if (b->staging_used) AKMC_CUDA(cudaEventSynchronize(b->staging_done));
-    uint64_t* tg = (uint64_t*)b->staging;
-    int32_t* order = (int32_t*)(b->staging + sizeof(uint64_t) * b->n);
+    const int slot = b->stage;
+    b->stage = (b->stage + 1) % akmc_batch::kStage;
+    if (b->staging_used[slot]) AKMC_CUDA(cudaEventSynchronize(b->staging_done[slot]));
+    char* stg = b->staging + (sizeof(uint64_t) + sizeof(int32_t)) * b->n * slot;
+    uint64_t* tg = (uint64_t*)stg;
+    int32_t* order = (int32_t*)(stg + sizeof(uint64_t) * b->n);
     std::vector<std::pair<double, int32_t>> work(b->n);
     for (int32_t v = 0; v < b->n; ++v) {
         tg[v] = n_events[v];
@@ -509,12 +567,13 @@ akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream str
     }
     std::stable_sort(work.begin(), work.end());   // largest expected work first
     for (int32_t v = 0; v < b->n; ++v) order[v] = work[v].second;
-    AKMC_CUDA(cudaMemcpyAsync(b->base + b->lo.targets, b->staging,
-                              (sizeof(uint64_t) + sizeof(int32_t)) * b->n, cudaMemcpyHostToDevice, s));
-    AKMC_CUDA(cudaEventRecord(b->staging_done, s));
-    b->staging_used = true;
+    AKMC_CUDA(cudaMemcpyAsync(b->base + b->lo.targets, stg, (sizeof(uint64_t) + sizeof(int32_t)) * b->n,
+                              cudaMemcpyHostToDevice, s));
+    AKMC_CUDA(cudaEventRecord(b->staging_done[slot], s));
+    b->staging_used[slot] = true;
     AKMC_CUDA(cudaMemsetAsync(b->base + b->lo.queue, 0, sizeof(uint32_t), s));
-    int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P);
+    if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P);
+    int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy[b->warps];
     if (per_sm < 1) per_sm = 1;
     int grid = std::min<long long>((long long)per_sm * b->n_sm, b->n);
     cudaError_t e = launch_step(b->args(), b->warps, grid, s);
@@ -555,7 +614,7 @@ akmc_status akmc_load_state(akmc_batch* b, int32_t voxel, const uint8_t* species
     if (!b || !species || !vac_pos) return fail(AKMC_EINVAL, "NULL argument");
     if (voxel < 0 || voxel >= b->n) return fail(AKMC_EINVAL, "voxel %d out of range", voxel);
     cudaStream_t s = (cudaStream_t)stream;
-    VoxelDev V = b->vox_host[voxel];
+    const VoxelDev& V = b->vox_host[voxel];
     int nvac = 0;
     for (int i = 0; i < V.N; ++i) {
         if (species[i] > kVac) return fail(AKMC_EINVAL, "species code %d at site %d", species[i], i);
@@ -567,19 +626,69 @@ akmc_status akmc_load_state(akmc_batch* b, int32_t voxel, const uint8_t* species
             return fail(AKMC_EINVAL, "vac_pos[%d] is not a vacancy site", q);
     if (!std::isfinite(t_hi) || !std::isfinite(t_lo)) return fail(AKMC_EINVAL, "clock must be finite");
     AKMC_CUDA(cudaStreamSynchronize(s));
-    V.t_hi = t_hi;
-    V.t_lo = t_lo;
-    V.n_events = n_events;
-    V.status = AKMC_OK;
+    double* io = (double*)(b->base + b->lo.io);
+    const double clk[2] = {t_hi, t_lo};
     AKMC_CUDA(cudaMemcpyAsync(V.species, species, V.N, cudaMemcpyHostToDevice, s));
     AKMC_CUDA(cudaMemcpyAsync(V.vac_pos, vac_pos, 4 * (size_t)V.nv, cudaMemcpyHostToDevice, s));
-    AKMC_CUDA(cudaMemsetAsync(V.vac_disp, 0, 12 * (size_t)V.nv, s));
-    AKMC_CUDA(cudaMemcpyAsync(b->base + b->lo.vox + sizeof(VoxelDev) * voxel, &V, sizeof V,
-                              cudaMemcpyHostToDevice, s));
+    AKMC_CUDA(cudaMemcpyAsync(io, clk, sizeof clk, cudaMemcpyHostToDevice, s));
+    AKMC_CUDA(cudaMemcpyAsync(io + 2, &n_events, sizeof n_events, cudaMemcpyHostToDevice, s));
+    AKMC_CUDA(launch_voxel_load((VoxelDev*)(b->base + b->lo.vox) + voxel, io, s));
     AKMC_CUDA(cudaStreamSynchronize(s));
     b->dirty = true;
     return AKMC_OK;
 }
+
+akmc_status akmc_load_batch_state(akmc_batch* b, const uint8_t* species, const int32_t* vac_pos,
+                                  const double* t_hi, const double* t_lo, const uint64_t* n_events,
+                                  akmc_stream stream) {
+    if (!b || !species || !vac_pos) return fail(AKMC_EINVAL, "NULL argument");
+    if ((t_hi == nullptr) != (t_lo == nullptr)) return fail(AKMC_EINVAL, "give both t_hi and t_lo or neither");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = b->n;
+    double* io = (double*)(b->base + b->lo.io);
+    AKMC_CUDA(cudaMemcpyAsync(b->base + b->lo.b_species, species, b->lo.tot_N, cudaMemcpyHostToDevice, s));
+    AKMC_CUDA(cudaMemcpyAsync(b->base + b->lo.b_pos, vac_pos, sizeof(int32_t) * b->lo.tot_nv,
+                              cudaMemcpyHostToDevice, s));
+    if (t_hi) {
+        AKMC_CUDA(cudaMemcpyAsync(io, t_hi, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        AKMC_CUDA(cudaMemcpyAsync(io + n, t_lo, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    }
+    if (n_events)
+        AKMC_CUDA(cudaMemcpyAsync(io + 2 * n, n_events, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+    AKMC_CUDA(launch_batch_load((VoxelDev*)(b->base + b->lo.vox), io, n, t_hi != nullptr, n_events != nullptr, s));
+    b->dirty = true;
+    return AKMC_OK;
+}
+
+akmc_status akmc_read_batch_state(akmc_batch* b, uint8_t* species, int32_t* vac_pos, int32_t* vac_disp,
+                                  double* t_hi, double* t_lo, uint64_t* n_events, int32_t* status,
+                                  akmc_stream stream) {
+    if (!b) return fail(AKMC_EINVAL, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = b->n;
+    double* io = (double*)(b->base + b->lo.io);
+    if (species)
+        AKMC_CUDA(cudaMemcpyAsync(species, b->base + b->lo.b_species, b->lo.tot_N, cudaMemcpyDeviceToHost, s));
+    if (vac_pos)
+        AKMC_CUDA(cudaMemcpyAsync(vac_pos, b->base + b->lo.b_pos, sizeof(int32_t) * b->lo.tot_nv,
+                                  cudaMemcpyDeviceToHost, s));
+    if (vac_disp)
+        AKMC_CUDA(cudaMemcpyAsync(vac_disp, b->base + b->lo.b_disp, sizeof(int32_t) * 3 * b->lo.tot_nv,
+                                  cudaMemcpyDeviceToHost, s));
+    if (t_hi || t_lo || n_events || status) {
+        AKMC_CUDA(launch_batch_read((const VoxelDev*)(b->base + b->lo.vox), io, n, s));
+        if (t_hi) AKMC_CUDA(cudaMemcpyAsync(t_hi, io, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (t_lo) AKMC_CUDA(cudaMemcpyAsync(t_lo, io + n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (n_events)
+            AKMC_CUDA(cudaMemcpyAsync(n_events, io + 2 * n, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
+        if (status)
+            AKMC_CUDA(cudaMemcpyAsync(status, io + 3 * n, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    }
+    return AKMC_OK;
+}
+
+size_t akmc_batch_sites(const akmc_batch* b) { return b ? b->lo.tot_N : 0; }
+int64_t akmc_batch_vacancies(const akmc_batch* b) { return b ? (int64_t)b->lo.tot_nv : 0; }
 
 akmc_status akmc_sync_status(akmc_batch* b, akmc_stream stream, int32_t* per_voxel) {
     if (!b) return fail(AKMC_EINVAL, "batch is NULL");
@@ -630,10 +739,11 @@ int32_t akmc_n_voxels(const akmc_batch* b) { return b ? b->n : 0; }
 
 void akmc_destroy_batch(akmc_batch* b) {
     if (!b) return;
-    if (b->staging_done) {
-        cudaEventSynchronize(b->staging_done);
-        cudaEventDestroy(b->staging_done);
-    }
+    for (int i = 0; i < akmc_batch::kStage; ++i)
+        if (b->staging_done[i]) {
+            cudaEventSynchronize(b->staging_done[i]);
+            cudaEventDestroy(b->staging_done[i]);
+        }
     if (b->staging) cudaFreeHost(b->staging);
     delete b;
 }

@@ -159,6 +159,79 @@ __global__ void place_kernel(VoxelDev* vox, int n_vox) {
     }
 }
 
+// Whole-batch state load: patch clock and counter from the io staging area
+// ([t_hi n][t_lo n][n_events n]), restart displacements, and validate each
+// voxel's lattice (codes <= 4, vacancy count, vac_pos names distinct vacancy
+// sites).  A voxel that fails gets status EINVAL and is skipped by the
+// kernels; one that passes gets status OK.
+__global__ void batch_load_kernel(VoxelDev* vox, const double* io, int n, int has_t, int has_n) {
+    __shared__ int bad, nvac;
+    VoxelDev& V = vox[blockIdx.x];
+    if (threadIdx.x == 0) { bad = 0; nvac = 0; }
+    __syncthreads();
+    int local = 0, lbad = 0;
+    for (int i = threadIdx.x; i < V.N; i += blockDim.x) {
+        int s = V.species[i];
+        lbad |= s > kVac;
+        local += s == kVac;
+    }
+    for (int q = threadIdx.x; q < V.nv; q += blockDim.x) {
+        int p = V.vac_pos[q];
+        if (p < 0 || p >= V.N || V.species[p] != kVac) lbad = 1;
+        for (int r = q + 1; r < V.nv; ++r) lbad |= V.vac_pos[r] == p;
+    }
+    for (int i = threadIdx.x; i < 3 * V.nv; i += blockDim.x) V.vac_disp[i] = 0;
+    if (lbad) atomicExch(&bad, 1);
+    atomicAdd(&nvac, local);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (has_t) {
+            V.t_hi = io[blockIdx.x];
+            V.t_lo = io[n + blockIdx.x];
+        }
+        if (has_n) V.n_events = ((const uint64_t*)io)[2 * n + blockIdx.x];
+        V.status = (bad || nvac != V.nv) ? kEINVAL : kOK;
+    }
+}
+
+// One voxel's state load (lattice validated on the host): clock and counter
+// from io ([t_hi, t_lo, n_events]), displacements restarted, status OK.
+__global__ void voxel_load_kernel(VoxelDev* V, const double* io) {
+    for (int i = threadIdx.x; i < 3 * V->nv; i += blockDim.x) V->vac_disp[i] = 0;
+    if (threadIdx.x == 0) {
+        V->t_hi = io[0];
+        V->t_lo = io[1];
+        V->n_events = ((const uint64_t*)io)[2];
+        V->status = kOK;
+    }
+}
+
+cudaError_t launch_voxel_load(VoxelDev* V, const double* io, cudaStream_t st) {
+    voxel_load_kernel<<<1, 128, 0, st>>>(V, io);
+    return cudaGetLastError();
+}
+
+// Whole-batch state read: clock, counter and status of every voxel into io
+// ([t_hi n][t_lo n][n_events n][status n as int32]).
+__global__ void batch_read_kernel(const VoxelDev* vox, double* io, int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        io[v] = vox[v].t_hi;
+        io[n + v] = vox[v].t_lo;
+        ((uint64_t*)io)[2 * n + v] = vox[v].n_events;
+        ((int32_t*)(io + 3 * n))[v] = vox[v].status;
+    }
+}
+
+cudaError_t launch_batch_load(VoxelDev* vox, const double* io, int n, int has_t, int has_n, cudaStream_t st) {
+    batch_load_kernel<<<n, 256, 0, st>>>(vox, io, n, has_t, has_n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_read(const VoxelDev* vox, double* io, int n, cudaStream_t st) {
+    batch_read_kernel<<<(n + 127) / 128, 128, 0, st>>>(vox, io, n);
+    return cudaGetLastError();
+}
+
 void launch_setup_model(ModelDev* M, int32_t* batch_status, int has_eam, int n_rho, cudaStream_t st) {
     int blocks = has_eam ? (4 * n_rho + 255) / 256 : 1;
     if (blocks < 1) blocks = 1;

@@ -3,18 +3,39 @@
 // (a8) and the compensated clock (a9), as one persistent kernel that steps a
 // whole voxel per CTA, plus the full rebuild used by akmc_compute_rates.
 //
+// Design for GB300: a dependent float64 operation costs ~64 cycles there
+// (float32: ~4.5), exp(double) ~1.1k and log(double) ~2.1k cycles, while an L2
+// hit costs ~290.  The chain of one event is therefore kept off the FP64 pipe
+// wherever the arithmetic allows:
+//  * energies are exact integers (pair model: 2^-24 eV; EAM split precision:
+//    2^-40 eV fixed point plus an FP32 polynomial part, rounded to 2^-24 eV);
+//  * rates come from per-voxel tables of exp(-beta * Ea) on the 2^-25 eV grid
+//    (two dependent FP64 multiplies instead of exp);
+//  * selection compares non-negative doubles as integers (IEEE order);
+//  * -ln(u2)/R of each event is batched and evaluated lane-parallel every
+//    kClockBatch events, then folded into the compensated clock;
+//  * the next event's Philox block is computed by an idle warp, with the
+//    uniforms built from integers;
+//  * the moved vacancy's read set is gathered before the event's density
+//    updates (whose change it adds locally), so gathers never wait on atomics;
+//  * hop terms are spread over all threads and summed as exact integers
+//    (pair: 2^-24 eV; EAM split: 2^-40 eV), so the sums are order-free.
+//
 // One CTA owns one voxel at a time and runs all of its requested events; the
-// voxel's rates, rate tree and vacancy coordinates live in shared memory while
-// it is resident.  Rating the 8 hops of one vacancy is done by warps: warp k
-// (mod the CTA's warp count) rates hop k with a fixed lane -> term mapping and
-// a fixed shuffle reduction, so results do not depend on the launch shape.
+// voxel's rates, rate tree, tables and vacancy coordinates live in shared
+// memory while it is resident.  Every result is independent of the launch
+// shape: integer sums are order-free, and the FP64 mode rates hop k in one
+// warp with a fixed lane mapping and shuffle tree.
 #include "akmc_device.cuh"
 #include "akmc_launch.h"
 
 namespace akmc {
 
+constexpr int kClockBatch = 128;
+
 struct __align__(16) StepShared {
     double E0[4];
+    double two_E0[4];
     double nu;
     double inv_knot;
     double phi_d[10][8];
@@ -24,23 +45,32 @@ struct __align__(16) StepShared {
     const long long* Fq;
     int32_t eps_q[2][25];
     int32_t fq[5][8];
+    int32_t thr_hi[4], thr_lo[4];
     int32_t sph[64];
     int32_t off[160];
     uint32_t ent[8][80];
     int32_t mk[8];
-    int32_t n_rho, shift, cur_model, vid;
+    uint8_t dsh[160][8];
+    int32_t n_rho, shift, cur_model, cur_small, vid;
     float inv_knot_f;
     VoxelDev v;
     uint64_t target;
-    // staging of one vacancy's read set
+    // staging of one vacancy's read set and its per-hop sums
+    long long fsite[160];     // F_{s_u}(rho_u) of every read site (split mode, 2^-40 eV)
     int32_t srho[160];
     uint8_t ssp[160];
-    double hop_de[8];
-    int32_t hop_A[8];
+    uint8_t fbad[160];
+    long long acc64[8];       // split mode: dE of each hop in 2^-40 eV
+    int32_t acc32[8];         // pair model: dE of each hop in 2^-24 eV
+    double hop_de[8];         // FP64 mode
     int32_t hop_bad[8];
-    // current event
-    double R, u2, t_hi, t_lo;
+    // clock batch: u2 and R of each event, then dt in place of u2
+    double cu2[kClockBatch];
+    double cR[kClockBatch];
+    double t_hi, t_lo;
+    double nu1, nu2;      // uniforms of the next event
     uint64_t n;
+    int32_t ccount;
     int32_t stop, numeric, n_aff;
     int32_t slot, dir, A;
     int32_t wX, wY, wZ, mX, mY, mZ;
@@ -50,6 +80,8 @@ struct Dyn {
     double* tree;
     double* rates;
     double* dE;
+    double* hsum;     // per vacancy: [1] vacancy sum, [2..3] half sums, [4..7] pair sums
+    double* etab;
     int32_t* pos;
     int32_t* X;
     int32_t* Y;
@@ -61,33 +93,54 @@ struct Dyn {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P) {
-    Dyn d;
+// Offsets of the dynamic shared-memory arrays (16-byte aligned).
+struct DynLayout {
+    size_t off[12];
+    size_t total;
+};
+
+__host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P) {
+    const size_t sz[12] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
+                           sizeof(double) * 8 * max_nv, sizeof(double) * 8 * max_nv,
+                           sizeof(double) * kEtab,      sizeof(int32_t) * max_nv,
+                           sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
+                           sizeof(int32_t) * max_nv,    sizeof(int32_t) * 3 * max_nv,
+                           sizeof(int32_t) * max_nv,    (size_t)8 * max_nv};
+    DynLayout l;
     size_t o = 0;
-    d.tree = (double*)(base + o);   o = align16(o + sizeof(double) * 2 * max_P);
-    d.rates = (double*)(base + o);  o = align16(o + sizeof(double) * 8 * max_nv);
-    d.dE = (double*)(base + o);     o = align16(o + sizeof(double) * 8 * max_nv);
-    d.pos = (int32_t*)(base + o);   o = align16(o + sizeof(int32_t) * max_nv);
-    d.X = (int32_t*)(base + o);     o = align16(o + sizeof(int32_t) * max_nv);
-    d.Y = (int32_t*)(base + o);     o = align16(o + sizeof(int32_t) * max_nv);
-    d.Z = (int32_t*)(base + o);     o = align16(o + sizeof(int32_t) * max_nv);
-    d.disp = (int32_t*)(base + o);  o = align16(o + sizeof(int32_t) * 3 * max_nv);
-    d.aff = (int32_t*)(base + o);   o = align16(o + sizeof(int32_t) * max_nv);
-    d.hop_sp = (uint8_t*)(base + o);
+    for (int i = 0; i < 12; ++i) {
+        l.off[i] = o;
+        o = align16(o + sz[i]);
+    }
+    l.total = o;
+    return l;
+}
+
+__device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P) {
+    const DynLayout l = dyn_layout(max_nv, max_P);
+    Dyn d;
+    d.tree = (double*)(base + l.off[0]);
+    d.rates = (double*)(base + l.off[1]);
+    d.dE = (double*)(base + l.off[2]);
+    d.hsum = (double*)(base + l.off[3]);
+    d.etab = (double*)(base + l.off[4]);
+    d.pos = (int32_t*)(base + l.off[5]);
+    d.X = (int32_t*)(base + l.off[6]);
+    d.Y = (int32_t*)(base + l.off[7]);
+    d.Z = (int32_t*)(base + l.off[8]);
+    d.disp = (int32_t*)(base + l.off[9]);
+    d.aff = (int32_t*)(base + l.off[10]);
+    d.hop_sp = (uint8_t*)(base + l.off[11]);
     return d;
 }
 
-size_t step_dyn_smem(int max_nv, int max_P) {
-    size_t o = 0;
-    o = align16(o + sizeof(double) * 2 * max_P);
-    o = align16(o + sizeof(double) * 8 * max_nv);
-    o = align16(o + sizeof(double) * 8 * max_nv);
-    for (int i = 0; i < 4; ++i) o = align16(o + sizeof(int32_t) * max_nv);
-    o = align16(o + sizeof(int32_t) * 3 * max_nv);
-    o = align16(o + sizeof(int32_t) * max_nv);
-    o = align16(o + 8 * max_nv);
-    return o;
+size_t step_dyn_smem(int max_nv, int max_P) { return dyn_layout(max_nv, max_P).total; }
+
+// Order of non-negative doubles equals the order of their bit patterns.
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+    return __double_as_longlong(a) < __double_as_longlong(b);
 }
+__device__ __forceinline__ bool is_zero(double a) { return __double_as_longlong(a) == 0; }
 
 template <int NW>
 __device__ void load_model(StepShared& S, const ModelDev* M) {
@@ -98,7 +151,12 @@ __device__ void load_model(StepShared& S, const ModelDev* M) {
         S.phi_d[i / 8][i % 8] = M->phi_d[i / 8][i % 8];
         S.phi_q[i / 8][i % 8] = M->phi_q[i / 8][i % 8];
     }
-    if (tid < 4) S.E0[tid] = M->E0[tid];
+    if (tid < 4) {
+        S.E0[tid] = M->E0[tid];
+        S.two_E0[tid] = M->two_E0[tid];
+        S.thr_hi[tid] = M->thr_hi[tid];
+        S.thr_lo[tid] = M->thr_lo[tid];
+    }
     if (tid == 0) {
         S.nu = M->nu;
         S.Fd = M->Fd;
@@ -109,14 +167,16 @@ __device__ void load_model(StepShared& S, const ModelDev* M) {
         S.inv_knot = M->inv_knot;
         S.inv_knot_f = (float)M->inv_knot;
         S.cur_model = -1;
+        S.cur_small = -1;
     }
 }
 
-// Stencil tables of the voxel's energy model (reloaded only when it changes).
+// Stencil tables of the voxel's energy model (reloaded only when the model or
+// the L = 4 special case changes).
 template <int NW>
-__device__ void load_tables(StepShared& S, const Tables* T, int model) {
+__device__ void load_tables(StepShared& S, const Tables* T, int model, int small) {
     const int tid = threadIdx.x;
-    if (S.cur_model == model) return;   // uniform: read after a barrier
+    if (S.cur_model == model && S.cur_small == small) return;   // uniform: read after a barrier
     __syncthreads();
     if (model == 0) {
         for (int i = tid; i < 64; i += NW * 32) S.off[i] = T->pair_off[i];
@@ -127,24 +187,30 @@ __device__ void load_tables(StepShared& S, const Tables* T, int model) {
         for (int i = tid; i < 8 * 80; i += NW * 32) S.ent[i / 80][i % 80] = T->eam_ent[i / 80][i % 80];
         if (tid < 8) S.mk[tid] = T->eam_mk[tid];
         for (int i = tid; i < 64; i += NW * 32) S.sph[i] = T->sph_off[i];
+        for (int i = tid; i < 160 * 8; i += NW * 32) S.dsh[i / 8][i % 8] = T->eam_dsh[small][i / 8][i % 8];
     }
     __syncthreads();
-    if (tid == 0) S.cur_model = model;
+    if (tid == 0) {
+        S.cur_model = model;
+        S.cur_small = small;
+    }
     __syncthreads();
 }
 
 // Embedding function on the fixed-point density r: knot k = r >> shift,
 // t = (r - k*2^shift) 2^-shift (exact).  Outside the table: clamp, flag.
-__device__ __forceinline__ void embed_split(const StepShared& S, int a, int r, long long& kq, float& p,
-                                            int& bad) {
+// Split precision: the knot value is exact in 2^-40 eV; the Hermite part
+// t (c1 + t (c2 + t c3)) is evaluated in FP32 (|part| < 0.5 eV) and rounded
+// to 2^-32 eV; the result is one integer in units of 2^-40 eV.
+__device__ __forceinline__ long long embed_q(const StepShared& S, int a, int r, int& bad) {
     const int last = S.n_rho - 1;
     int k = r >> S.shift;
     if (r < 0 || k > last || (k == last && (r & ((1 << S.shift) - 1)))) bad = 1;
     k = min(max(k, 0), last - 1);
-    float t = (float)(r - (k << S.shift)) * S.inv_knot_f;
-    float4 c = __ldg(&S.Ff[a * last + k]);
-    p = t * (c.x + t * (c.y + t * c.z));
-    kq = __ldg(&S.Fq[a * S.n_rho + k]);
+    const float t = (float)(r - (k << S.shift)) * S.inv_knot_f;
+    const float4 c = __ldg(&S.Ff[a * last + k]);
+    const float p = t * (c.x + t * (c.y + t * c.z));
+    return __ldg(&S.Fq[a * S.n_rho + k]) + ((long long)__float2int_rn(p * 4294967296.0f) << 8);
 }
 
 __device__ __forceinline__ double embed_fp64(const StepShared& S, int a, int r, int& bad) {
@@ -157,132 +223,302 @@ __device__ __forceinline__ double embed_fp64(const StepShared& S, int a, int r, 
     return c.F + t * (c.c1 + t * (c.c2 + t * c.c3));
 }
 
-// (a2)-(a5) Rates of the 8 hops of vacancy q, its leaf sum and tree path.
-template <int NW>
-__device__ void refresh(StepShared& S, const Dyn& D, int q) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// (a4) Barrier Ea = max(0, dE, E0[A] + dE/2) and rate nu * exp(-beta Ea) of one
+// hop.  With y = dE/2 + 2 (middle branch, constant K = nu exp(beta (2 - E0))) or
+// y = dE (Ea = dE branch, K = nu), rate = K exp(-beta y); for 0 <= y < 4 eV,
+// exp(-beta y) is the product of three table entries indexed by the 27 bits of
+// y * 2^25 (times a 3rd-order correction for a float64 dE that is not on the
+// grid).  Other y, or tables that over/underflow, use exp directly.
+// On the grid (dE = q 2^-24 eV) the branch choice and indexing are integer
+// selects, so the 8 lanes do not diverge.
+__device__ __forceinline__ double hop_rate_grid(const StepShared& S, const Dyn& D, int A, int q) {
+    const int Ai = A < 4 ? A : 3;
+    if (!S.v.etab_ok) {
+        const double de = (double)q * 0x1p-24;
+        const double Ea = fmax(fmax(0.0, de), S.E0[Ai] + 0.5 * de);
+        return A == kVac ? 0.0 : S.nu * exp(-(Ea * S.v.beta));
+    }
+    const bool zero = q < S.thr_lo[Ai], up = q > S.thr_hi[Ai];
+    const long long j = zero ? 0 : (up ? 2LL * q : (long long)q + (1LL << 26));
+    const double K = (zero || up) ? S.nu : D.etab[1536 + Ai];
+    double g;
+    if (j >= 0 && j < (1LL << 27)) {
+        const int ji = (int)j;
+        g = (K * D.etab[ji & 511]) * (D.etab[512 + ((ji >> 9) & 511)] * D.etab[1024 + (ji >> 18)]);
+    } else {
+        g = K * exp(-(S.v.beta * ((double)j * 0x1p-25)));
+    }
+    return A == kVac ? 0.0 : g;
+}
+
+__device__ __forceinline__ double hop_rate_fp64(const StepShared& S, const Dyn& D, int A, double de) {
+    if (A == kVac) return 0.0;
+    if (!S.v.etab_ok) {
+        const double Ea = fmax(fmax(0.0, de), S.E0[A] + 0.5 * de);
+        return S.nu * exp(-(Ea * S.v.beta));
+    }
+    if (de < -S.two_E0[A]) return S.nu;
+    double K, y;
+    if (de > S.two_E0[A]) { K = S.nu; y = de; } else { K = D.etab[1536 + A]; y = fma(de, 0.5, 2.0); }
+    const double yj = y * 0x1p25;
+    if (!(yj >= 0.0 && yj < 134217728.0)) return K * exp(-(S.v.beta * y));
+    const int j = (int)yj;
+    const double r = fma(-(double)j, 0x1p-25, y);
+    const double x = S.v.beta * r;
+    const double corr = fma(fma(fma(-x, 0.16666666666666666, 0.5), x, -1.0), x, 1.0);
+    return (K * D.etab[j & 511]) * ((D.etab[512 + ((j >> 9) & 511)] * D.etab[1024 + (j >> 18)]) * corr);
+}
+
+__device__ __forceinline__ bool finite_bits(double g) {
+    return ((__double_as_longlong(g) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// Uniforms of event n built from the Philox block with integer operations
+// (exact: a 53-bit integer times 2^-53).
+__device__ __forceinline__ double u53_to_double(uint64_t a) {
+    if (a == 0) return 0.0;
+    const int e = 63 - __clzll((long long)a);           // top bit position, <= 53
+    const uint64_t mant = (a << (52 - e)) & 0xFFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(((uint64_t)(e - 53 + 1023) << 52) | mant));
+}
+
+__device__ __forceinline__ void next_uniforms(StepShared& S) {
+    const uint64_t n = S.n, uid = S.v.uid, seed = S.v.seed;
+    uint32_t c0 = (uint32_t)n, c1 = (uint32_t)(n >> 32), c2 = (uint32_t)uid,
+             c3 = (uint32_t)(uid >> 32) & 0x7fffffffu;
+    philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    S.nu1 = u53_to_double(((uint64_t)c0 << 21) | (c1 >> 11));
+    S.nu2 = u53_to_double((((uint64_t)c2 << 21) | (c3 >> 11)) + 1);
+}
+
+// ---- (a2)-(a5): rates of the 8 hops of one vacancy, in phases ----------------
+// G  gather the read set (all threads);
+// F  split precision: embedding value of every read site (all threads);
+// E  hop energy changes (all threads) and, for the vacancy that just moved,
+//    this event's density updates (a7);
+// R  rates, subtree sums and tree path (lanes 0..7 of warp 0).
+// A barrier separates G, F, E and R.  For the vacancy that just moved (w ->
+// m) the read set is gathered before this event's density updates reach
+// memory and the hop's density change is added locally.
+
+template <int NW, int MODE>
+__device__ __forceinline__ void phase_gather(StepShared& S, const Dyn& D, int q, bool moved) {
+    constexpr int NT = NW * 32;
+    constexpr bool eam = MODE != 0;
+    constexpr int U = eam ? kEamU : kPairU;
+    const int tid = threadIdx.x;
     const int L = S.v.L, M2 = 2 * L;
     const int X = D.X[q], Y = D.Y[q], Z = D.Z[q];
-    const bool eam = S.v.model == 1;
-    const int U = eam ? kEamU : kPairU;
-    // gather the read set
-    for (int u = tid; u < U; u += NW * 32) {
-        int o = S.off[u];
-        int s = site_index(wrap_coord(X + off_dx(o), M2), wrap_coord(Y + off_dy(o), M2),
-                           wrap_coord(Z + off_dz(o), M2), L);
+    if (moved && tid == NT - 1) next_uniforms(S);   // the next event's Philox block, off the critical path
+    for (int u = tid; u < U; u += NT) {
+        const int o = S.off[u];
+        const int s = site_index(wrap_coord(X + off_dx(o), M2), wrap_coord(Y + off_dy(o), M2),
+                                 wrap_coord(Z + off_dz(o), M2), L);
         S.ssp[u] = S.v.species[s];
-        if (eam) S.srho[u] = S.v.rho[s];
-    }
-    __syncthreads();
-    for (int k = warp; k < 8; k += NW) {
-        const int A = S.ssp[S.mk[k]];
-        if (A == kVac) {
-            if (lane == 0) { S.hop_A[k] = kVac; S.hop_de[k] = 0.0; S.hop_bad[k] = 0; }
-            continue;
+        if (eam) {
+            int r = S.v.rho[s];
+            if (moved) {
+                const int ds = S.dsh[u][S.dir];
+                r += S.fq[S.A][ds >> 3] - S.fq[S.A][ds & 7];
+            }
+            S.srho[u] = r;
         }
-        if (!eam) {
-            // (a2) dE = sum over the 13 bonds of w (V -> A) and 13 bonds of m (A -> V),
-            // exact integer arithmetic in units of 2^-24 eV.
-            int acc = 0;
-            if (lane < kPairE) {
-                uint32_t e = S.ent[k][lane];
-                int idx = e & 0xff, sh = (e >> 8) & 1, side = (e >> 9) & 1;
-                int x = S.ssp[idx];
-                int t = S.eps_q[sh][A * 5 + x] - S.eps_q[sh][kVac * 5 + x];
-                acc = side ? -t : t;
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) { S.hop_de[k] = (double)acc * 0x1p-24; S.hop_A[k] = A; S.hop_bad[k] = 0; }
-        } else if (S.v.precision == 1) {
-            // (a3) split precision: knot values and pair terms exact in 2^-40 eV,
-            // the Hermite polynomial part in FP32, assembled in FP64.
-            long long aq = 0;
-            float af = 0.f;
+    }
+    if (tid < 8) {
+        S.acc64[tid] = 0;
+        S.acc32[tid] = 0;
+        S.hop_bad[tid] = 0;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void phase_site_embed(StepShared& S) {
+    for (int u = threadIdx.x; u < kEamU; u += NW * 32) {
+        const int a = S.ssp[u];
+        int bad = 0;
+        S.fsite[u] = a == kVac ? 0 : embed_q(S, a, S.srho[u], bad);
+        S.fbad[u] = (uint8_t)bad;
+    }
+}
+
+template <int NW, int MODE>
+__device__ __forceinline__ void phase_terms(StepShared& S, bool moved) {
+    constexpr int NT = NW * 32;
+    constexpr bool eam = MODE != 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (MODE == 0) {
+        // (a2) dE = sum over the 13 bonds of w (V -> A) and 13 bonds of m (A -> V),
+        // exact integers in units of 2^-24 eV (order-free accumulation).
+        for (int it = tid; it < 8 * kPairE; it += NT) {
+            const int k = it / kPairE, e = it - k * kPairE;
+            const int A = S.ssp[S.mk[k]];
+            if (A == kVac) continue;
+            const uint32_t en = S.ent[k][e];
+            const int x = S.ssp[en & 0xff], sh = (en >> 8) & 1;
+            const int t = S.eps_q[sh][A * 5 + x] - S.eps_q[sh][kVac * 5 + x];
+            atomicAdd(&S.acc32[k], (en >> 9) & 1 ? -t : t);
+        }
+    } else if (MODE == 1) {
+        // (a3) dE = sum_i [F(rho_i + drho_i) - F(rho_i)] + own term + pair terms,
+        // every term an integer in 2^-40 eV; one warp per hop, integer shuffle sum.
+        for (int k = warp; k < 8; k += NW) {
+            const int A = S.ssp[S.mk[k]];
+            if (A == kVac) continue;
+            long long v = 0;
             int bad = 0;
-            for (int j = lane; j < kEamE; j += 32) {
-                uint32_t e = S.ent[k][j];
-                int a, r0, r1;
-                if (e >> 14) {
-                    a = A;
-                    r0 = S.srho[S.mk[k]];
-                    r1 = S.srho[0] - S.fq[A][1];
+            for (int e = lane; e < kEamE; e += 32) {
+                const uint32_t en = S.ent[k][e];
+                if (en >> 14) {
+                    const int mk = S.mk[k];
+                    v += embed_q(S, A, S.srho[0] - S.fq[A][1], bad) - S.fsite[mk];
+                    bad |= S.fbad[mk];
                 } else {
-                    int idx = e & 0xff, sip = (e >> 8) & 7, sim = (e >> 11) & 7;
-                    a = S.ssp[idx];
+                    const int idx = en & 0xff, sip = (en >> 8) & 7, sim = (en >> 11) & 7;
+                    const int a = S.ssp[idx];
                     if (a == kVac) continue;
-                    r0 = S.srho[idx];
-                    r1 = r0 + S.fq[A][sip] - S.fq[A][sim];
-                    int pi = pair_index(A, a);
-                    aq += S.phi_q[pi][sip] - S.phi_q[pi][sim];
+                    const int pi = pair_index(A, a);
+                    v += embed_q(S, a, S.srho[idx] + S.fq[A][sip] - S.fq[A][sim], bad) - S.fsite[idx] +
+                         (S.phi_q[pi][sip] - S.phi_q[pi][sim]);
+                    bad |= S.fbad[idx];
                 }
-                long long q0, q1;
-                float p0, p1;
-                embed_split(S, a, r1, q1, p1, bad);
-                embed_split(S, a, r0, q0, p0, bad);
-                aq += q1 - q0;
-                af += p1 - p0;
             }
-            aq = warp_sum(aq);
-            af = warp_sum(af);
+            v = warp_sum(v);
             bad = __any_sync(0xffffffffu, bad);
             if (lane == 0) {
-                S.hop_de[k] = (double)aq * 0x1p-40 + (double)af;
-                S.hop_A[k] = A;
+                S.acc64[k] = v;
                 S.hop_bad[k] = bad;
             }
-        } else {
-            // (a3) FP64 throughout.
+        }
+    } else {
+        // (a3) FP64 throughout: one warp per hop, fixed lane order and shuffle tree.
+        for (int k = warp; k < 8; k += NW) {
+            const int A = S.ssp[S.mk[k]];
+            if (A == kVac) {
+                if (lane == 0) S.hop_de[k] = 0.0;
+                continue;
+            }
             double acc = 0.0;
             int bad = 0;
             for (int j = lane; j < kEamE; j += 32) {
-                uint32_t e = S.ent[k][j];
+                const uint32_t en = S.ent[k][j];
                 int a, r0, r1;
                 double ph = 0.0;
-                if (e >> 14) {
+                if (en >> 14) {
                     a = A;
                     r0 = S.srho[S.mk[k]];
                     r1 = S.srho[0] - S.fq[A][1];
                 } else {
-                    int idx = e & 0xff, sip = (e >> 8) & 7, sim = (e >> 11) & 7;
+                    const int idx = en & 0xff, sip = (en >> 8) & 7, sim = (en >> 11) & 7;
                     a = S.ssp[idx];
                     if (a == kVac) continue;
                     r0 = S.srho[idx];
                     r1 = r0 + S.fq[A][sip] - S.fq[A][sim];
-                    int pi = pair_index(A, a);
+                    const int pi = pair_index(A, a);
                     ph = S.phi_d[pi][sip] - S.phi_d[pi][sim];
                 }
                 acc += (embed_fp64(S, a, r1, bad) - embed_fp64(S, a, r0, bad)) + ph;
             }
             acc = warp_sum(acc);
             bad = __any_sync(0xffffffffu, bad);
-            if (lane == 0) { S.hop_de[k] = acc; S.hop_A[k] = A; S.hop_bad[k] = bad; }
+            if (lane == 0) {
+                S.hop_de[k] = acc;
+                S.hop_bad[k] = bad;
+            }
         }
     }
-    __syncthreads();
-    // (a4) barriers and rates of the 8 hops in lanes 0..7 of warp 0, (a5) the
-    // vacancy sum ((g0+g1)+(g2+g3))+((g4+g5)+(g6+g7)) and its tree path.
-    if (warp == 0 && lane < 8) {
-        const int A = S.hop_A[lane];
-        const double de = S.hop_de[lane];
-        int bad = S.hop_bad[lane];
-        double g = 0.0;
-        if (A != kVac) {
-            double Ea = fmax(fmax(0.0, de), S.E0[A] + 0.5 * de);
-            g = S.nu * exp(-(Ea * S.v.beta));
-            if (!isfinite(g)) bad = 1;
+    // (a7) this event's density updates, now that the read set is in shared memory:
+    // rho_i += f_A(r_iw) over S(w), -= f_A(r_im) over S(m).
+    if (eam && moved) {
+        const int L = S.v.L, M2 = 2 * L;
+        for (int i = tid; i < 2 * kSph; i += NT) {
+            const int side = i >= kSph;
+            const int o = S.sph[side ? i - kSph : i];
+            const int cX = side ? S.mX : S.wX, cY = side ? S.mY : S.wY, cZ = side ? S.mZ : S.wZ;
+            const int s = site_index(wrap_coord(cX + off_dx(o), M2), wrap_coord(cY + off_dy(o), M2),
+                                     wrap_coord(cZ + off_dz(o), M2), L);
+            const int f = S.fq[S.A][off_extra(o)];
+            atomicAdd(&S.v.rho[s], side ? -f : f);
         }
+    }
+}
+
+// R: (a4) rates of the 8 hops in lanes 0..7 of warp 0; (a5) subtree sums
+// (g0+g1), (g2+g3), ..., ((g0+g1)+(g2+g3)), ((g4+g5)+(g6+g7)), the vacancy sum
+// and its tree path.  Only warp 0 executes this; it ends with __syncwarp.
+template <int MODE>
+__device__ __forceinline__ void phase_rates(StepShared& S, const Dyn& D, int q) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 8) {
+        const int A = S.ssp[S.mk[lane]];
+        double de, g;
+        if (MODE == 2) {
+            de = S.hop_de[lane];
+            g = hop_rate_fp64(S, D, A, de);
+        } else {
+            const int dq = MODE == 0 ? S.acc32[lane] : (int)((S.acc64[lane] + (1LL << 15)) >> 16);
+            de = A == kVac ? 0.0 : (double)dq * 0x1p-24;
+            g = hop_rate_grid(S, D, A, dq);
+        }
+        int bad = S.hop_bad[lane] | !finite_bits(g);
+        const double s1 = g + __shfl_xor_sync(0xffu, g, 1);
+        const double s2 = s1 + __shfl_xor_sync(0xffu, s1, 2);
+        const double s3 = s2 + __shfl_xor_sync(0xffu, s2, 4);
+        bad = __any_sync(0xffu, bad);
         D.rates[8 * q + lane] = g;
         D.dE[8 * q + lane] = de;
         D.hop_sp[8 * q + lane] = (uint8_t)A;
-        double s1 = g + __shfl_xor_sync(0xffu, g, 1);
-        double s2 = s1 + __shfl_xor_sync(0xffu, s1, 2);
-        double s3 = s2 + __shfl_xor_sync(0xffu, s2, 4);
-        bad = __any_sync(0xffu, bad);
+        double* h = D.hsum + 8 * q;
+        if ((lane & 1) == 0) h[4 + (lane >> 1)] = s1;
+        if ((lane & 3) == 0) h[2 + (lane >> 2)] = s2;
         if (lane == 0) {
+            h[1] = s3;
             const int P = S.v.P;
             D.tree[P + q] = s3;
             for (int i = (P + q) >> 1; i >= 1; i >>= 1) D.tree[i] = D.tree[2 * i] + D.tree[2 * i + 1];
             if (bad) S.numeric = 1;
+        }
+    }
+    __syncwarp();
+}
+
+// Full refresh of one vacancy with barriers (rebuild, and vacancies other
+// than the moved one).
+template <int NW, int MODE>
+__device__ void refresh_full(StepShared& S, const Dyn& D, int q) {
+    phase_gather<NW, MODE>(S, D, q, false);
+    __syncthreads();
+    if (MODE == 1) {
+        phase_site_embed<NW>(S);
+        __syncthreads();
+    }
+    phase_terms<NW, MODE>(S, false);
+    __syncthreads();
+    if (threadIdx.x < 32) phase_rates<MODE>(S, D, q);
+    __syncthreads();
+}
+
+// (a9) dt = -ln(u2)/R of the batched events, evaluated lane-parallel, summed
+// pairwise (relative error below 10 ulp of the batch sum), and folded into
+// the Neumaier-compensated clock (t_hi, t_lo).
+template <int NW>
+__device__ void flush_clock(StepShared& S) {
+    const int tid = threadIdx.x;
+    const int cnt = S.ccount;
+    if (cnt == 0) return;   // uniform
+    for (int i = tid; i < cnt; i += NW * 32) S.cu2[i] = -log(S.cu2[i]) / S.cR[i];
+    __syncthreads();
+    if (tid < 32) {
+        double s = 0.0;
+        for (int i = tid; i < cnt; i += 32) s += S.cu2[i];
+        s = warp_sum(s);
+        if (tid == 0) {
+            const double hi = S.t_hi + s;
+            if (fabs(S.t_hi) >= fabs(s))
+                S.t_lo += (S.t_hi - hi) + s;
+            else
+                S.t_lo += (s - hi) + S.t_hi;
+            S.t_hi = hi;
+            S.ccount = 0;
         }
     }
     __syncthreads();
@@ -308,13 +544,28 @@ __device__ void load_voxel_state(StepShared& S, const Dyn& D) {
         D.hop_sp[i] = V.hop_sp[i];
     }
     for (int i = tid; i < 2 * V.P; i += NW * 32) D.tree[i] = V.tree[i];
+    for (int i = tid; i < kEtab; i += NW * 32) D.etab[i] = V.etab[i];
+    for (int q = tid; q < V.nv; q += NW * 32) {
+        const double* g = V.rates + 8 * q;
+        double* h = D.hsum + 8 * q;
+        h[4] = g[0] + g[1];
+        h[5] = g[2] + g[3];
+        h[6] = g[4] + g[5];
+        h[7] = g[6] + g[7];
+        h[2] = h[4] + h[5];
+        h[3] = h[6] + h[7];
+        h[1] = h[2] + h[3];
+    }
     if (tid == 0) {
         S.t_hi = V.t_hi;
         S.t_lo = V.t_lo;
         S.n = V.n_events;
         S.stop = 0;
         S.numeric = 0;
+        S.ccount = 0;
     }
+    __syncthreads();
+    if (tid == 0) next_uniforms(S);
 }
 
 template <int NW>
@@ -337,120 +588,122 @@ __device__ void store_voxel_state(StepShared& S, const Dyn& D, VoxelDev* gv) {
     }
 }
 
-// Events of the resident voxel (a6 -> a7 -> a9 -> a8), target of them at most.
-template <int NW>
+// (a6) select with u1 * R (descent compares as integers) and (a7) apply the
+// swap; executed by lane 0 of warp 0.  Returns false if the voxel is trapped
+// or a numeric error was flagged.
+__device__ __forceinline__ bool select_and_swap(StepShared& S, const Dyn& D) {
+    const double R = D.tree[1];
+    if (S.numeric) {
+        S.v.status = kENUMERIC;
+        return false;
+    }
+    if (!(__double_as_longlong(R) > 0)) {
+        S.v.status = kETRAPPED;
+        return false;
+    }
+    double t = S.nu1 * R;
+    const int P = S.v.P;
+    int node = 1;
+    while (node < P) {
+        const double l = D.tree[2 * node], r = D.tree[2 * node + 1];
+        if (lt_nonneg(t, l) || is_zero(r)) {
+            node = 2 * node;
+        } else {
+            t -= l;
+            node = 2 * node + 1;
+        }
+    }
+    const int slot = node - P;
+    const double* hp = D.hsum + 8 * slot;
+    const double* gp = D.rates + 8 * slot;
+    const double h2 = hp[2], h3 = hp[3], h4 = hp[4], h5 = hp[5], h6 = hp[6], h7 = hp[7];
+    const double g0 = gp[0], g1 = gp[1], g2 = gp[2], g3 = gp[3], g4 = gp[4], g5 = gp[5], g6 = gp[6], g7 = gp[7];
+    const unsigned long long hops = *(const unsigned long long*)(D.hop_sp + 8 * slot);
+    const int wX = D.X[slot], wY = D.Y[slot], wZ = D.Z[slot], w = D.pos[slot];
+    int d = 0;
+    if (!(lt_nonneg(t, h2) || is_zero(h3))) { t -= h2; d = 4; }
+    const double l2 = d ? h6 : h4, r2 = d ? h7 : h5;
+    if (!(lt_nonneg(t, l2) || is_zero(r2))) { t -= l2; d += 2; }
+    const double l3 = d == 0 ? g0 : d == 2 ? g2 : d == 4 ? g4 : g6;
+    const double r3 = d == 0 ? g1 : d == 2 ? g3 : d == 4 ? g5 : g7;
+    if (!(lt_nonneg(t, l3) || is_zero(r3))) d += 1;
+    const int L = S.v.L, M2 = 2 * L;
+    const int dx = (d & 1) ? -1 : 1, dy = (d & 2) ? -1 : 1, dz = (d & 4) ? -1 : 1;
+    const int mX = wrap_coord(wX + dx, M2), mY = wrap_coord(wY + dy, M2), mZ = wrap_coord(wZ + dz, M2);
+    const int m = site_index(mX, mY, mZ, L);
+    const int A = (int)((hops >> (8 * d)) & 0xff);
+    S.v.species[w] = (uint8_t)A;
+    S.v.species[m] = (uint8_t)kVac;
+    S.slot = slot;
+    S.dir = d;
+    S.A = A;
+    S.wX = wX; S.wY = wY; S.wZ = wZ;
+    S.mX = mX; S.mY = mY; S.mZ = mZ;
+    S.n_aff = 0;
+    D.pos[slot] = m;
+    D.X[slot] = mX;
+    D.Y[slot] = mY;
+    D.Z[slot] = mZ;
+    D.disp[3 * slot + 0] += dx;
+    D.disp[3 * slot + 1] += dy;
+    D.disp[3 * slot + 2] += dz;
+    const int c = S.ccount;
+    S.cu2[c] = S.nu2;
+    S.cR[c] = R;
+    S.ccount = c + 1;
+    if (S.v.log_cap > 0) S.v.log[S.n % (uint64_t)S.v.log_cap] = 8 * slot + d;
+    S.n += 1;
+    return true;
+}
+
+// Events of the resident voxel (a6 -> a7 -> a8, a9 batched), target at most.
+// Per event: [warp 0: select + swap] B [gather, affected list, next Philox]
+// B ([site embedding] B) [hop terms, density updates] B [warp 0: rates + tree];
+// warp 0 goes straight on to the next select, so the rates of event n and the
+// selection of event n+1 need no CTA-wide barrier between them.
+template <int NW, int MODE>
 __device__ void run_events(StepShared& S, const Dyn& D, uint64_t target) {
     const int tid = threadIdx.x;
-    const int clock_tid = NW > 1 ? 32 : 0;
     const int L = S.v.L, M2 = 2 * L;
-    const bool eam = S.v.model == 1;
-    const int reach = eam ? 8 : 4;
+    constexpr int reach = MODE != 0 ? 8 : 4;
+    int ccount = S.ccount;   // uniform copy of the clock-batch fill
     for (uint64_t done = 0; done < target; ++done) {
-        // (a6) select with u1 * R; (a7) swap; bookkeeping.
-        if (tid == 0) {
-            const double R = D.tree[1];
-            if (!(R > 0.0)) {
-                S.stop = 1;
-                S.v.status = kETRAPPED;
-            } else {
-                double u1, u2;
-                event_uniforms(S.v.seed, S.v.uid, S.n, u1, u2);
-                double t = u1 * R;
-                const int P = S.v.P;
-                int node = 1;
-                while (node < P) {
-                    double l = D.tree[2 * node], r = D.tree[2 * node + 1];
-                    if (t < l || r == 0.0) {
-                        node = 2 * node;
-                    } else {
-                        t -= l;
-                        node = 2 * node + 1;
-                    }
-                }
-                const int slot = node - P;
-                const double* g = D.rates + 8 * slot;
-                const double a01 = g[0] + g[1], a23 = g[2] + g[3], a45 = g[4] + g[5], a67 = g[6] + g[7];
-                const double b0 = a01 + a23, b1 = a45 + a67;
-                int d = 0;
-                if (!(t < b0 || b1 == 0.0)) { t -= b0; d = 4; }
-                double l2 = d ? a45 : a01, r2 = d ? a67 : a23;
-                if (!(t < l2 || r2 == 0.0)) { t -= l2; d += 2; }
-                double l3 = g[d], r3 = g[d + 1];
-                if (!(t < l3 || r3 == 0.0)) { d += 1; }
-                const int dx = (d & 1) ? -1 : 1, dy = (d & 2) ? -1 : 1, dz = (d & 4) ? -1 : 1;
-                const int wX = D.X[slot], wY = D.Y[slot], wZ = D.Z[slot];
-                const int mX = wrap_coord(wX + dx, M2), mY = wrap_coord(wY + dy, M2),
-                          mZ = wrap_coord(wZ + dz, M2);
-                const int w = D.pos[slot];
-                const int m = site_index(mX, mY, mZ, L);
-                const int A = D.hop_sp[8 * slot + d];
-                S.v.species[w] = (uint8_t)A;
-                S.v.species[m] = (uint8_t)kVac;
-                D.pos[slot] = m;
-                D.X[slot] = mX;
-                D.Y[slot] = mY;
-                D.Z[slot] = mZ;
-                D.disp[3 * slot + 0] += dx;
-                D.disp[3 * slot + 1] += dy;
-                D.disp[3 * slot + 2] += dz;
-                if (S.v.log_cap > 0) S.v.log[S.n % (uint64_t)S.v.log_cap] = 8 * slot + d;
-                S.n += 1;
-                S.R = R;
-                S.u2 = u2;
-                S.slot = slot;
-                S.dir = d;
-                S.A = A;
-                S.wX = wX; S.wY = wY; S.wZ = wZ;
-                S.mX = mX; S.mY = mY; S.mZ = mZ;
-                S.n_aff = 0;
-            }
-        }
+        if (tid == 0) S.stop = !select_and_swap(S, D);
         __syncthreads();
         if (S.stop) break;
-        // (a9) dt = -ln(u2)/R, Neumaier-compensated (t_hi, t_lo).
-        if (tid == clock_tid) {
-            const double dt = -log(S.u2) / S.R;
-            const double s = S.t_hi + dt;
-            if (fabs(S.t_hi) >= fabs(dt))
-                S.t_lo += (S.t_hi - s) + dt;
-            else
-                S.t_lo += (dt - s) + S.t_hi;
-            S.t_hi = s;
-        }
-        // (a7) EAM densities: rho_i += f_A(r_iw) over S(w), -= f_A(r_im) over S(m).
-        if (eam) {
-            for (int i = tid; i < 2 * kSph; i += NW * 32) {
-                const int side = i >= kSph;
-                const int o = S.sph[side ? i - kSph : i];
-                const int cX = side ? S.mX : S.wX, cY = side ? S.mY : S.wY, cZ = side ? S.mZ : S.wZ;
-                const int s = site_index(wrap_coord(cX + off_dx(o), M2), wrap_coord(cY + off_dy(o), M2),
-                                         wrap_coord(cZ + off_dz(o), M2), L);
-                const int f = S.fq[S.A][off_extra(o)];
-                atomicAdd(&S.v.rho[s], side ? -f : f);
-            }
-        }
-        // (a8) vacancies whose read set may contain a changed site: the moved
-        // one and every vacancy within `reach` half units of w per axis.
+        ++ccount;
+        // (a8) other vacancies whose read set may contain a changed site: every
+        // vacancy within `reach` half units of w per axis.
         for (int q = tid; q < S.v.nv; q += NW * 32) {
-            bool hit = q == S.slot;
-            if (!hit) {
-                int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
-                ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
-                ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
-                ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
-                hit = abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach;
-            }
-            if (hit) D.aff[atomicAdd(&S.n_aff, 1)] = q;
+            if (q == S.slot) continue;
+            int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
+            ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
+            ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
+            ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
+            if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach) D.aff[atomicAdd(&S.n_aff, 1)] = q;
         }
+        phase_gather<NW, MODE>(S, D, S.slot, true);
         __syncthreads();
+        if (MODE == 1) {
+            phase_site_embed<NW>(S);
+            __syncthreads();
+        }
+        phase_terms<NW, MODE>(S, true);
+        __syncthreads();
+        if (tid < 32) phase_rates<MODE>(S, D, S.slot);
         const int n_aff = S.n_aff;
-        for (int i = 0; i < n_aff; ++i) refresh<NW>(S, D, D.aff[i]);
-        if (S.numeric) {
-            if (tid == 0) S.v.status = kENUMERIC;
-            break;
+        if (n_aff > 0) {
+            __syncthreads();
+            for (int i = 0; i < n_aff; ++i) refresh_full<NW, MODE>(S, D, D.aff[i]);
+        }
+        if (ccount == kClockBatch) {
+            flush_clock<NW>(S);
+            ccount = 0;
         }
     }
     __syncthreads();
+    if (tid == 0 && S.numeric && S.v.status == kOK) S.v.status = kENUMERIC;
+    flush_clock<NW>(S);
 }
 
 template <int NW>
@@ -473,10 +726,16 @@ __global__ void __launch_bounds__(NW * 32) step_kernel(BatchArgs a) {
         const int vid = S.vid;
         if (vid < 0) break;
         if (S.v.status == kOK && S.target > 0) {
-            load_tables<NW>(S, a.tab, S.v.model);
+            load_tables<NW>(S, a.tab, S.v.model, S.v.L == 4);
             load_voxel_state<NW>(S, D);
             __syncthreads();
-            run_events<NW>(S, D, S.target);
+            const int mode = S.v.model == 0 ? 0 : (S.v.precision == 1 ? 1 : 2);
+            if (mode == 0)
+                run_events<NW, 0>(S, D, S.target);
+            else if (mode == 1)
+                run_events<NW, 1>(S, D, S.target);
+            else
+                run_events<NW, 2>(S, D, S.target);
             store_voxel_state<NW>(S, D, &a.vox[vid]);
         }
         __syncthreads();
@@ -495,19 +754,54 @@ __global__ void __launch_bounds__(NW * 32) rebuild_kernel(BatchArgs a) {
     if (threadIdx.x == 0) S.v = a.vox[blockIdx.x];
     __syncthreads();
     if (S.v.status == kEINVAL) return;   // placement failed; uniform
-    load_tables<NW>(S, a.tab, S.v.model);
+    load_tables<NW>(S, a.tab, S.v.model, S.v.L == 4);
     load_voxel_state<NW>(S, D);
     for (int i = threadIdx.x; i < 2 * S.v.P; i += NW * 32) D.tree[i] = 0.0;
     __syncthreads();
-    for (int q = 0; q < S.v.nv; ++q) refresh<NW>(S, D, q);
+    const int mode = S.v.model == 0 ? 0 : (S.v.precision == 1 ? 1 : 2);
+    for (int q = 0; q < S.v.nv; ++q) {
+        if (mode == 0)
+            refresh_full<NW, 0>(S, D, q);
+        else if (mode == 1)
+            refresh_full<NW, 1>(S, D, q);
+        else
+            refresh_full<NW, 2>(S, D, q);
+    }
     if (threadIdx.x == 0 && S.numeric) S.v.status = kENUMERIC;
     __syncthreads();
     store_voxel_state<NW>(S, D, &a.vox[blockIdx.x]);
 }
 
+// Per-voxel rate tables (see kEtab); etab_ok = 0 if any entry over- or underflows.
+__global__ void rate_table_kernel(VoxelDev* vox, const ModelDev* M) {
+    __shared__ int ok;
+    VoxelDev& V = vox[blockIdx.x];
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kEtab; i += blockDim.x) {
+        double v;
+        if (i < 1536) {
+            const int k = i >> 9, idx = i & 511;
+            const double y = (double)idx * ldexp(1.0, 9 * k - 25);
+            v = exp(-(V.beta * y));
+        } else {
+            v = M->nu * exp(V.beta * (2.0 - M->E0[i - 1536]));
+        }
+        V.etab[i] = v;
+        if (!isfinite(v) || !(v >= 2.2250738585072014e-308)) ok = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) V.etab_ok = ok;
+}
+
 template <int NW>
 static cudaError_t set_smem(const void* fn, size_t dyn) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, cudaStream_t st) {
+    rate_table_kernel<<<n_vox, 256, 0, st>>>(vox, M);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st) {

@@ -234,3 +234,39 @@ def test_full_size_batched_eam_sampled(model):
         assert np.abs(g["dE"] - o.state()["dE"]).max() <= SPLIT_DE_TOL
         _assert_rates(g["rates"], o.state()["rates"], rtol=1e-3)
         assert _time(g) > 0
+
+
+def test_batch_state_roundtrip_and_validation(model):
+    descs = _mixed_descs()
+    b = Batch(descs, model, event_log_capacity=600)
+    b.step(300)
+    host = b.host_buffers(pinned=True)
+    b.read_batch_state(host)
+    torch.cuda.synchronize()
+    off = 0
+    voff = 0
+    for v, d in enumerate(descs):
+        s = b.read_state(v)
+        N = 2 * d.L ** 3
+        assert np.array_equal(host["species"][off:off + N], s["species"])
+        assert np.array_equal(host["vac_pos"][voff:voff + d.n_vac], s["vac_pos"])
+        assert host["t_hi"][v] == s["t_hi"] and host["n_events"][v] == s["n_events"] == 300
+        off += N
+        voff += d.n_vac
+    # reload the same state into a fresh batch: it continues identically
+    c = Batch(descs, model, event_log_capacity=600)
+    c.load_batch_state(host["species"], host["vac_pos"], host["t_hi"], host["t_lo"], host["n_events"])
+    c.step(300)
+    b.step(300)
+    for v in range(len(descs)):
+        g1, g2 = b.read_state(v, log=True), c.read_state(v, log=True)
+        assert np.array_equal(g1["species"], g2["species"])
+        assert g1["t_hi"] == g2["t_hi"] and g1["t_lo"] == g2["t_lo"]
+        assert np.array_equal(g1["event_log"][300:600], g2["event_log"][300:600])
+    # a vacancy slot that does not name a vacancy site is rejected on the device
+    bad_pos = host["vac_pos"].copy()
+    bad_pos[0] = (bad_pos[0] + 1) % 54
+    c.load_batch_state(host["species"], bad_pos)
+    c.step(10)
+    st, per = c.sync_status()
+    assert per[0] == 1 and (per[1:] == 0).all()
