@@ -196,6 +196,7 @@ def main():
     ap.add_argument("--events", type=int, default=1_000_000, help="events per voxel per step")
     ap.add_argument("--ref-events", type=int, default=20000, help="oracle events per core per step")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/rate-kernel/cpu legs")
+    ap.add_argument("--launch", default=None, help="warps,ctas_per_sm of the step kernel (skips the tuner)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -218,7 +219,10 @@ def main():
         descs = [synth.VoxelDesc(d.L, d.n_vac, d.frac, d.T, d.model, d.precision,
                                  synth.splitmix64(synth.SEED_BASE + 2, d.uid + rank * N_VOX), d.uid + rank * N_VOX)
                  for d in descs]
-    warps, per_sm = T.tune(descs, model, events=3000)
+    if args.launch:
+        warps, per_sm = (int(x) for x in args.launch.split(","))
+    else:
+        warps, per_sm = T.tune(descs, model, events=3000)
     b = Batch(descs, model)
     b.set_launch(warps, per_sm)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

@@ -8,7 +8,9 @@
 // neighbours with shared-memory atomics (integer, hence order-independent).
 // Global traffic is one read of the haloed species tile (row by row, one
 // 32-byte sector per warp access) and one coalesced write of the density
-// tile; index arithmetic is per row, not per site.
+// tile.  The non-Fe sites of each slab of halo rows are first compacted into
+// a list (ballot, one append per warp), then one warp per listed site adds
+// its 58 corrections (distinct targets, so lanes never conflict).
 #include "akmc_device.cuh"
 #include "akmc_launch.h"
 
@@ -16,12 +18,16 @@ namespace akmc {
 
 constexpr int kDensThreads = 256;
 constexpr int kDensWarps = kDensThreads / 32;
+constexpr int kSlabRows = 64;                                   // halo rows compacted per pass
+constexpr int kListCap = kSlabRows * 2 * (kTX + 2 * kHalo);     // every site of a slab
 
 __global__ void __launch_bounds__(kDensThreads) density_kernel(const VoxelDev* vox, const ModelDev* M,
                                                                const Tables* tab, const int4* items) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t s_off[64];
     __shared__ int32_t s_cq[5][8];
+    __shared__ uint16_t s_list[kListCap];
+    __shared__ int s_nlist;
     const int4 it = items[blockIdx.x];
     const VoxelDev& V = vox[it.x];
     const int L = V.L;
@@ -34,6 +40,7 @@ __global__ void __launch_bounds__(kDensThreads) density_kernel(const VoxelDev* v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < kSph) s_off[tid] = tab->sph_off[tid];
     if (tid < 40) s_cq[tid / 8][tid % 8] = M->cq[tid / 8][tid % 8];
+    if (tid == 0) s_nlist = 0;
     const int32_t rho0 = M->rho_pure;
     const uint8_t* sp = V.species;
     // haloed species tile, one row (fixed y, z) per warp iteration
@@ -51,16 +58,30 @@ __global__ void __launch_bounds__(kDensThreads) density_kernel(const VoxelDev* v
     }
     for (int i = tid; i < tz * ty * trow; i += kDensThreads) rt[i] = rho0;
     __syncthreads();
-    // scatter corrections of every non-Fe site of the haloed tile
-    for (int r = warp; r < hz * hy; r += kDensWarps) {
-        const int cy = r % hy, cz = r / hy;
-        const uint8_t* src = hs + r * hrow;
-        for (int c = lane; c < hrow; c += 32) {
-            const int s = src[c];
-            if (s == kFe) continue;
+    const int n_rows = hz * hy;
+    for (int r0 = 0; r0 < n_rows; r0 += kSlabRows) {
+        const int r1 = min(n_rows, r0 + kSlabRows);
+        for (int r = r0 + warp; r < r1; r += kDensWarps) {
+            const uint8_t* src = hs + r * hrow;
+            for (int c0 = 0; c0 < hrow; c0 += 32) {
+                const int c = c0 + lane;
+                const bool hit = c < hrow && src[c] != kFe;
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                int base = 0;
+                if (lane == 0 && m) base = atomicAdd(&s_nlist, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (hit) s_list[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((r - r0) * hrow + c);
+            }
+        }
+        __syncthreads();
+        const int nl = s_nlist;
+        for (int i = warp; i < nl; i += kDensWarps) {
+            const int rel = s_list[i];
+            const int rr = r0 + rel / hrow, c = rel % hrow;
+            const int s = hs[rr * hrow + c];
             const int b = c & 1;
-            const int HX = c, HY = 2 * cy + b, HZ = 2 * cz + b;   // half-unit coordinates in the halo frame
-            for (int k = 0; k < kSph; ++k) {
+            const int HX = c, HY = 2 * (rr % hy) + b, HZ = 2 * (rr / hy) + b;   // half units, halo frame
+            for (int k = lane; k < kSph; k += 32) {
                 const int o = s_off[k];
                 const int X = HX + off_dx(o), Y = HY + off_dy(o), Z = HZ + off_dz(o);
                 if (X < 0 || Y < 0 || Z < 0) continue;
@@ -69,8 +90,10 @@ __global__ void __launch_bounds__(kDensThreads) density_kernel(const VoxelDev* v
                 atomicAdd(&rt[(iz * ty + iy) * trow + 2 * ix + (X & 1)], s_cq[s][off_extra(o)]);
             }
         }
+        __syncthreads();
+        if (tid == 0) s_nlist = 0;
+        __syncthreads();
     }
-    __syncthreads();
     // coalesced write of the density tile, one row per warp iteration
     int32_t* rho = V.rho;
     for (int r = warp; r < tz * ty; r += kDensWarps) {
