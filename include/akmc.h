@@ -181,6 +181,30 @@ akmc_status akmc_sync_status(akmc_batch* batch, akmc_stream stream, int32_t* per
 akmc_status akmc_cluster_hist(akmc_batch* batch, int32_t voxel, int32_t mode,
                               int64_t hist[8], akmc_stream stream);
 
+/* Allocation-free Cu cluster histogram (no counterpart in the paper).
+ * For callers that cannot let a library allocate device memory: programs
+ * whose GPU memory is owned entirely by another allocator (a framework or
+ * simulation that reserves the device's memory up front and treats any
+ * other cudaMalloc as an error or a source of fragmentation), and code on a
+ * latency-critical path where an allocation could block or synchronise the
+ * device.  Same result as akmc_cluster_hist on a lattice that is not part of
+ * a batch: species is a device array of 2L^3 species codes (site order as
+ * above), hist a device int64[8] that receives the bin counts (mode and bins
+ * as akmc_cluster_hist).  The scratch (union-find labels and cluster sizes)
+ * is a fixed file-scope device array of 2 x 524,288 int32 (4 MiB) that every
+ * GPU which loads the library holds until the process exits; lattices above
+ * 524,288 sites (L > 64) are rejected with AKMC_EINVAL.  The call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  Its first
+ * call on a device does a one-time set-up there (device addresses of the
+ * static arrays and a copy of the neighbour tables into them), so make that
+ * first call before any stream capture.  Every call shares the scratch
+ * array, which keeps the last call's contents (each call re-initialises what
+ * it needs); calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race on it.  Stream-ordered; does not
+ * synchronise. */
+akmc_status akmc_cluster_hist_noalloc(const uint8_t* species, int32_t L, int32_t mode, int64_t* hist,
+                                      akmc_stream stream);
+
 /* Launch shape of akmc_step_n: warps per voxel-CTA (1, 2, 4 or 8) and CTAs
  * per SM (0 = as many as fit).  Results are identical for every shape. */
 akmc_status akmc_set_launch(akmc_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm);

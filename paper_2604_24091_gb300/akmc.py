@@ -73,6 +73,7 @@ def load_library():
             "akmc_batch_sites": (SZ, [P]),
             "akmc_batch_vacancies": (ctypes.c_int64, [P]),
             "akmc_cluster_hist": (I32, [P, I32, I32, P, P]),
+            "akmc_cluster_hist_noalloc": (I32, [P, I32, I32, P, P]),
             "akmc_set_launch": (I32, [P, I32, I32]),
             "akmc_n_voxels": (I32, [P]),
             "akmc_destroy_batch": (None, [P]),
@@ -141,6 +142,17 @@ def workspace_bytes(descs, model, event_log_capacity=0) -> int:
     if n == 0:
         raise AkmcError(EINVAL, last_error())
     return int(n)
+
+
+def cluster_hist_noalloc(species, L, mode, hist, stream=None):
+    """Allocation-free Cu cluster histogram of one lattice held by the caller:
+    `species` a CUDA uint8 tensor of 2L^3 codes, `hist` a CUDA int64 tensor of
+    8 bins that receives the counts (stream-ordered)."""
+    import torch
+    assert species.is_cuda and species.dtype == torch.uint8 and species.is_contiguous()
+    assert hist.is_cuda and hist.dtype == torch.int64 and hist.numel() >= 8
+    _check(load_library().akmc_cluster_hist_noalloc(ctypes.c_void_p(species.data_ptr()), int(L), int(mode),
+                                                    ctypes.c_void_p(hist.data_ptr()), _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):

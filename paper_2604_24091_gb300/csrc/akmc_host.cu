@@ -153,6 +153,13 @@ const Tables& tables() {
     return T;
 }
 
+}  // namespace
+
+const Tables& akmc::host_tables() { return tables(); }
+void akmc::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 // ---------------------------------------------------------------- validation
 
 int next_pow2(int n) {

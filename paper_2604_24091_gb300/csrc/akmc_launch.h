@@ -22,6 +22,8 @@ cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st
 cudaError_t launch_rebuild(const BatchArgs& a, int warps, cudaStream_t st);
 int step_occupancy(int warps, int max_nv, int max_P);
 
+const Tables& host_tables();   // stencil tables built on the host
+void set_last_error(const char* msg);   // text returned by akmc_last_error() on this thread
 cudaError_t launch_cluster(const VoxelDev* vox, int voxel, int N, const Tables* tab, int mode,
                            int32_t* labels, int32_t* sizes, unsigned long long* hist, cudaStream_t st);
 

@@ -4,6 +4,11 @@
 // parent pointer points to a smaller site index, links go from the larger
 // root to the smaller one with compare-and-swap, so every loop below ends
 // after at most N iterations.  Scratch: labels[N], sizes[N] (int32).
+#include <akmc.h>
+
+#include <mutex>
+#include <string>
+
 #include "akmc_device.cuh"
 #include "akmc_launch.h"
 
@@ -70,19 +75,93 @@ __global__ void cluster_bins(int N, const int32_t* lab, const int32_t* sizes, un
     }
 }
 
-cudaError_t launch_cluster(const VoxelDev* vox_host, int voxel, int N, const Tables* tab, int mode,
-                           int32_t* labels, int32_t* sizes, unsigned long long* hist, cudaStream_t st) {
-    const VoxelDev& V = vox_host[voxel];
+static cudaError_t launch_cluster_raw(const uint8_t* species, int L, int N, const Tables* tab, int mode,
+                                      int32_t* labels, int32_t* sizes, unsigned long long* hist, cudaStream_t st) {
     const int threads = 256;
     int blocks = (N + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     cudaError_t e = cudaMemsetAsync(hist, 0, 8 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    cluster_init<<<blocks, threads, 0, st>>>(V.species, N, labels, sizes);
-    cluster_hook<<<blocks, threads, 0, st>>>(V.species, V.L, N, tab, mode == 0 ? 14 : 8, labels);
+    cluster_init<<<blocks, threads, 0, st>>>(species, N, labels, sizes);
+    cluster_hook<<<blocks, threads, 0, st>>>(species, L, N, tab, mode == 0 ? 14 : 8, labels);
     cluster_count<<<blocks, threads, 0, st>>>(N, labels, sizes);
     cluster_bins<<<blocks, threads, 0, st>>>(N, labels, sizes, hist);
     return cudaGetLastError();
 }
 
+cudaError_t launch_cluster(const VoxelDev* vox_host, int voxel, int N, const Tables* tab, int mode,
+                           int32_t* labels, int32_t* sizes, unsigned long long* hist, cudaStream_t st) {
+    const VoxelDev& V = vox_host[voxel];
+    return launch_cluster_raw(V.species, V.L, N, tab, mode, labels, sizes, hist, st);
+}
+
 }  // namespace akmc
+
+// ---- allocation-free entry point ---------------------------------------------
+// Some callers cannot let a library allocate device memory: programs whose
+// GPU memory is owned entirely by another allocator (a framework or
+// simulation that reserves the device's memory up front and treats any other
+// cudaMalloc as an error or a source of fragmentation), and code on a
+// latency-critical path where an allocation may block or synchronise the
+// device.  For them the Cu cluster histogram has a variant whose scratch
+// (union-find labels and cluster sizes) is a fixed file-scope device array;
+// the caller passes only its input lattice and its output histogram.
+
+namespace {
+
+constexpr int kStaticMaxSites = 2 * 64 * 64 * 64;   // 524,288 sites: lattices up to L = 64
+static __device__ __align__(256) int32_t g_cluster_scratch[2 * kStaticMaxSites];
+static __device__ __align__(256) akmc::Tables g_static_tables;
+
+struct StaticSetup {
+    bool done = false;
+    int32_t* scratch = nullptr;
+    akmc::Tables* tables = nullptr;
+};
+std::mutex g_static_mu;
+StaticSetup g_static_setup[64];
+
+akmc_status static_fail(akmc_status st, const std::string& msg) {
+    akmc::set_last_error(msg.c_str());
+    return st;
+}
+
+}  // namespace
+
+extern "C" akmc_status akmc_cluster_hist_noalloc(const uint8_t* species, int32_t L, int32_t mode, int64_t* hist,
+                                                 akmc_stream stream) {
+    using namespace akmc;
+    if (!species || !hist) return static_fail(AKMC_EINVAL, "species or hist is NULL");
+    if (mode != 0 && mode != 1) return static_fail(AKMC_EINVAL, "mode must be 0 or 1");
+    if (L < 3 || 2LL * L * L * L > kStaticMaxSites)
+        return static_fail(AKMC_EINVAL, "L=" + std::to_string(L) + " outside [3, 64]: the static scratch holds " +
+                                             std::to_string(kStaticMaxSites) + " sites");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_fail(AKMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return static_fail(AKMC_EINVAL, "device ordinal above 63");
+    StaticSetup su;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        StaticSetup& s = g_static_setup[dev];
+        if (!s.done) {
+            // once per device, with that device current: device addresses of the
+            // static arrays, and the stencil tables copied into place
+            e = cudaGetSymbolAddress((void**)&s.scratch, g_cluster_scratch);
+            if (e != cudaSuccess)
+                return static_fail(AKMC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            e = cudaGetSymbolAddress((void**)&s.tables, g_static_tables);
+            if (e != cudaSuccess)
+                return static_fail(AKMC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            e = cudaMemcpy(s.tables, &host_tables(), sizeof(Tables), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return static_fail(AKMC_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+            s.done = true;
+        }
+        su = s;
+    }
+    const int N = 2 * L * L * L;
+    e = launch_cluster_raw(species, L, N, su.tables, mode, su.scratch, su.scratch + kStaticMaxSites,
+                           (unsigned long long*)hist, (cudaStream_t)stream);
+    if (e != cudaSuccess) return static_fail(AKMC_ECUDA, std::string("cluster kernels: ") + cudaGetErrorString(e));
+    return AKMC_OK;
+}
