@@ -197,13 +197,18 @@ def main():
     ap.add_argument("--ref-events", type=int, default=20000, help="oracle events per core per step")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/rate-kernel/cpu legs")
     ap.add_argument("--launch", default=None, help="warps,ctas_per_sm of the step kernel (skips the tuner)")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the serving workload (Poisson arrivals, continuous batching) instead")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.serving:
+        return serving(args)
 
     import torch
     import torch.distributed as dist
     from paper_2604_24091_gb300 import Batch
+    from paper_2604_24091_gb300 import shard as S
     from paper_2604_24091_gb300 import tune as T
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,10 +220,7 @@ def main():
     dev = torch.device("cuda", local)
     model = synth.default_model()
     descs = synth.config_batched_eam(N_VOX)
-    if rank:
-        descs = [synth.VoxelDesc(d.L, d.n_vac, d.frac, d.T, d.model, d.precision,
-                                 synth.splitmix64(synth.SEED_BASE + 2, d.uid + rank * N_VOX), d.uid + rank * N_VOX)
-                 for d in descs]
+    descs = S.rank_descs(descs, rank, lambda uid: synth.splitmix64(synth.SEED_BASE + 2, uid))
     if args.launch:
         warps, per_sm = (int(x) for x in args.launch.split(","))
     else:
@@ -251,11 +253,7 @@ def main():
     clocks = sampler.stop()
     st, per = b.sync_status()
     assert st == 0, "voxel status %s" % np.unique(per)
-    dev_time = sum(times)
-    if world > 1:
-        t = torch.tensor([dev_time], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_time = float(t.item())
+    dev_time = S.max_over_ranks(sum(times), dist if world > 1 else None, dev)
     events_total = float(E) * N_VOX * args.steps * world
     value = events_total / dev_time
     peak, peak_kind = _peaks()
@@ -348,6 +346,38 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
                            "sample": "%d voxels of the workload, one per host core, %d events each (%.1f s)"
                            % (procs, per, wall)}
     return out
+
+
+def serving(args):
+    """Serving workload: Poisson arrivals (200 requests/s for 10 s) of
+    batched-EAM-like voxels (32^3 cells, 1 vacancy, split precision), each
+    asking for 1e6-1e7 events (log-uniform), admitted under a 120 GB HBM
+    budget with continuous batching; then the same at 70% of the measured
+    capacity.  Reports p50/p99 latency per 1e6 events and events/s."""
+    import torch
+    from paper_2604_24091_gb300.serve import Request, Server, latency_summary
+    torch.cuda.set_device(0)
+    model = synth.default_model()
+    shape = synth.VoxelDesc(32, 1, (0.003, 0.007, 0.014), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT)
+    srv = Server(model, shape, hbm_budget=120e9, max_slots=2048, chunk=20000)
+    out = {"metric": METRIC + " (serving)", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "serving: Poisson 200 req/s for 10 s, 32^3-cell EAM voxels, 1e6-1e7 events "
+                      "each, 120 GB HBM budget", "slots": srv.n_slots, "bytes_per_slot": srv.bytes_per_slot,
+                      "chunk_events": srv.chunk}}
+    reqs = [Request(t, d, n, i) for i, (t, d, n) in enumerate(synth.serving_requests(10.0, 200.0))]
+    res, st = srv.run(reqs)
+    out["window"] = dict(latency_summary(res), events_per_s=st["events_per_s"], elapsed_s=st["elapsed_s"],
+                         requests_offered=len(reqs), offered_events=int(sum(r.n_events for r in reqs)))
+    cap = st["events"] / max(st["busy_s"], 1e-9)
+    mean_ev = float(np.mean([r.n_events for r in reqs]))
+    lam = 0.7 * cap / mean_ev
+    reqs70 = [Request(t, d, n, i) for i, (t, d, n) in
+              enumerate(synth.serving_requests(10.0, lam, seed=synth.SEED_BASE + 15))]
+    res70, st70 = srv.run(reqs70)
+    out["at_70pct_capacity"] = dict(latency_summary(res70), events_per_s=st70["events_per_s"],
+                                    rate_hz=lam, requests=len(reqs70), capacity_events_per_s=cap)
+    out["value"] = st["events_per_s"]
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -140,6 +140,27 @@ akmc_status akmc_compute_rates(akmc_batch* batch, akmc_stream stream);
  * Philox(seed, (n, uid)). */
 akmc_status akmc_step_n(akmc_batch* batch, const uint64_t* n_events, akmc_stream stream);
 
+/* The two halves of akmc_step_n, for CUDA-graph capture and chunked serving:
+ * akmc_set_targets copies n_events (host, n_voxels entries) and the processing
+ * order into the workspace (stream-ordered; the host array may be reused on
+ * return); akmc_launch_step resets the work queue and launches the persistent
+ * step kernel with the targets already on the device -- one memset and one
+ * kernel, so a stream capture of it replays "run the stored targets again".
+ * akmc_launch_step fails with AKMC_EINVAL while rates are out of date after
+ * a state load (call akmc_compute_rates first). */
+akmc_status akmc_set_targets(akmc_batch* batch, const uint64_t* n_events, akmc_stream stream);
+akmc_status akmc_launch_step(akmc_batch* batch, akmc_stream stream);
+
+/* Re-seed n voxel slots in place with new descriptors (continuous batching:
+ * a finished request's slot takes the next request).  Each new descriptor
+ * must keep the slot's L, n_vac, model and precision; T, composition, seed
+ * and uid may change.  The slot restarts at event 0 and time 0 with a fresh
+ * Philox placement, densities, rate tables, rates and tree; other voxels are
+ * untouched.  Stream-ordered with respect to earlier and later launches on
+ * the same stream; synchronises the stream before returning. */
+akmc_status akmc_reset_voxels(akmc_batch* batch, const int32_t* slots, const akmc_voxel_desc* descs,
+                              int32_t n, akmc_stream stream);
+
 /* Copy one voxel's state to host memory; synchronises the stream. */
 akmc_status akmc_read_state(akmc_batch* batch, int32_t voxel, akmc_state* out, akmc_stream stream);
 

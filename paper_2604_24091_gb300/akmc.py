@@ -64,6 +64,9 @@ def load_library():
             "akmc_workspace_bytes": (SZ, [P, I32, P, I32]),
             "akmc_create_batch": (I32, [P, I32, P, I32, P, SZ, P, ctypes.POINTER(P)]),
             "akmc_compute_rates": (I32, [P, P]),
+            "akmc_set_targets": (I32, [P, P, P]),
+            "akmc_launch_step": (I32, [P, P]),
+            "akmc_reset_voxels": (I32, [P, P, P, I32, P]),
             "akmc_step_n": (I32, [P, P, P]),
             "akmc_read_state": (I32, [P, I32, ctypes.POINTER(StateC), P]),
             "akmc_load_state": (I32, [P, I32, P, P, ctypes.c_double, ctypes.c_double, U64, P]),
@@ -208,6 +211,35 @@ class Batch:
         """Run n_events (scalar or one per voxel) further events per voxel."""
         arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))
         _check(self._lib.akmc_step_n(self._h, _ptr(arr), _stream_ptr(stream)))
+
+    def set_targets(self, n_events, stream=None):
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))
+        _check(self._lib.akmc_set_targets(self._h, _ptr(arr), _stream_ptr(stream)))
+
+    def launch_step(self, stream=None):
+        """Run the targets stored by set_targets (capturable in a CUDA graph)."""
+        _check(self._lib.akmc_launch_step(self._h, _stream_ptr(stream)))
+
+    def capture_step(self, n_events, stream=None):
+        """A torch CUDA graph whose replay runs n_events more events per voxel."""
+        import torch
+        s = stream if stream is not None else torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        self.set_targets(n_events, stream=s)   # outside the capture: copies targets, sets launch attributes
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.launch_step(stream=s)
+        return g
+
+    def reset_voxels(self, slots, descs, stream=None):
+        """Re-seed slots in place with new descriptors (same L, n_vac, model, precision)."""
+        sl = np.ascontiguousarray(slots, np.int32)
+        cd = make_descs(descs)
+        _check(self._lib.akmc_reset_voxels(self._h, _ptr(sl), ctypes.cast(cd, ctypes.c_void_p), int(sl.size),
+                                           _stream_ptr(stream)))
+        for s_, d in zip(sl.tolist(), descs):
+            self.descs[s_] = d
 
     def set_launch(self, warps: int, ctas_per_sm: int = 0):
         _check(self._lib.akmc_set_launch(self._h, int(warps), int(ctas_per_sm)))

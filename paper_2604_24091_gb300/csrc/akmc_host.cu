@@ -250,7 +250,7 @@ struct Layout {
     size_t phi_raw = 0, f_raw = 0, F_raw = 0, Fd = 0, Ff = 0, Fq = 0, items = 0;
     size_t labels = 0, sizes = 0, total = 0;
     std::vector<size_t> species, rho, pos, disp, rates, dE, hop, tree, log, etab;
-    size_t state_begin = 0, state_end = 0, io = 0;
+    size_t state_begin = 0, state_end = 0, io = 0, reset_list = 0, reset_items = 0;
     size_t b_species = 0, b_pos = 0, b_disp = 0, tot_N = 0, tot_nv = 0;
     std::vector<int4> item_list;
     int max_nv = 1, max_P = 1;
@@ -286,7 +286,9 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
                     for (int x = 0; x < L; x += kTX) Lo.item_list.push_back(make_int4(v, x, y, z));
         }
         Lo.items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
+        Lo.reset_items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
     }
+    Lo.reset_list = take(sizeof(int32_t) * n);
     Lo.io = take(32 * (size_t)n);
     // Per-voxel state, each kind concatenated in voxel order so that whole-batch
     // transfers are single copies.
@@ -383,7 +385,7 @@ akmc_status rebuild(akmc_batch* b, cudaStream_t st) {
                                        (int)b->lo.item_list.size(), st);
         if (e != cudaSuccess) return fail(AKMC_ECUDA, "density kernel: %s", cudaGetErrorString(e));
     }
-    cudaError_t e = launch_rebuild(a, 8, st);
+    cudaError_t e = launch_rebuild(a, 8, nullptr, 0, st);
     if (e != cudaSuccess) return fail(AKMC_ECUDA, "rebuild kernel: %s", cudaGetErrorString(e));
     b->dirty = false;
     return AKMC_OK;
@@ -532,9 +534,9 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
     launch_setup_model((ModelDev*)(b->base + lo.model), (int32_t*)(b->base + lo.status), has_eam,
                        has_eam ? m->n_rho : 0, s);
     AKMC_TRY(cudaGetLastError());
-    launch_place((VoxelDev*)(b->base + lo.vox), n, s);
+    launch_place((VoxelDev*)(b->base + lo.vox), n, nullptr, s);
     AKMC_TRY(cudaGetLastError());
-    AKMC_TRY(launch_rate_tables((VoxelDev*)(b->base + lo.vox), n, (const ModelDev*)(b->base + lo.model), s));
+    AKMC_TRY(launch_rate_tables((VoxelDev*)(b->base + lo.vox), n, (const ModelDev*)(b->base + lo.model), nullptr, s));
     // The pageable host images above must outlive their copies.
     AKMC_TRY(cudaStreamSynchronize(s));
 #undef AKMC_TRY
@@ -552,13 +554,9 @@ akmc_status akmc_compute_rates(akmc_batch* b, akmc_stream stream) {
     return rebuild(b, (cudaStream_t)stream);
 }
 
-akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream stream) {
+akmc_status akmc_set_targets(akmc_batch* b, const uint64_t* n_events, akmc_stream stream) {
     if (!b || !n_events) return fail(AKMC_EINVAL, "batch or n_events is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    if (b->dirty) {
-        akmc_status st = rebuild(b, s);
-        if (st != AKMC_OK) return st;
-    }
     const int slot = b->stage;
     b->stage = (b->stage + 1) % akmc_batch::kStage;
     if (b->staging_used[slot]) AKMC_CUDA(cudaEventSynchronize(b->staging_done[slot]));
@@ -578,13 +576,103 @@ akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream str
                               cudaMemcpyHostToDevice, s));
     AKMC_CUDA(cudaEventRecord(b->staging_done[slot], s));
     b->staging_used[slot] = true;
-    AKMC_CUDA(cudaMemsetAsync(b->base + b->lo.queue, 0, sizeof(uint32_t), s));
     if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P);
+    return AKMC_OK;
+}
+
+akmc_status akmc_launch_step(akmc_batch* b, akmc_stream stream) {
+    if (!b) return fail(AKMC_EINVAL, "batch is NULL");
+    if (b->dirty) return fail(AKMC_EINVAL, "rates are out of date after a state load: call akmc_compute_rates");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P);
+    AKMC_CUDA(cudaMemsetAsync(b->base + b->lo.queue, 0, sizeof(uint32_t), s));
     int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy[b->warps];
     if (per_sm < 1) per_sm = 1;
     int grid = std::min<long long>((long long)per_sm * b->n_sm, b->n);
     cudaError_t e = launch_step(b->args(), b->warps, grid, s);
     if (e != cudaSuccess) return fail(AKMC_ECUDA, "step kernel: %s", cudaGetErrorString(e));
+    return AKMC_OK;
+}
+
+akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream stream) {
+    if (!b || !n_events) return fail(AKMC_EINVAL, "batch or n_events is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->dirty) {
+        akmc_status st = rebuild(b, s);
+        if (st != AKMC_OK) return st;
+    }
+    akmc_status st = akmc_set_targets(b, n_events, stream);
+    if (st != AKMC_OK) return st;
+    return akmc_launch_step(b, stream);
+}
+
+akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_voxel_desc* descs, int32_t n,
+                              akmc_stream stream) {
+    if (!b || (n > 0 && (!slots || !descs))) return fail(AKMC_EINVAL, "NULL argument");
+    if (n < 0 || n > b->n) return fail(AKMC_EINVAL, "bad slot count %d", n);
+    if (n == 0) return AKMC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<char> seen(b->n, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t v = slots[i];
+        if (v < 0 || v >= b->n || seen[v]) return fail(AKMC_EINVAL, "slot %d out of range or repeated", v);
+        seen[v] = 1;
+        const akmc_voxel_desc& d = descs[i];
+        const akmc_voxel_desc& o = b->desc[v];
+        if (d.L != o.L || d.n_vac != o.n_vac || d.model != o.model || d.precision != o.precision)
+            return fail(AKMC_EINVAL, "slot %d: a new voxel must keep L, n_vac, model and precision", v);
+        if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(AKMC_EINVAL, "slot %d: bad T", v);
+        int32_t cnt[4];
+        for (int k = 0; k < 3; ++k)
+            if (!(d.frac[k] >= 0.0) || !(d.frac[k] <= 1.0)) return fail(AKMC_EINVAL, "slot %d: bad frac", v);
+        species_counts(d, cnt);
+        if ((long long)cnt[0] + cnt[1] + cnt[2] + cnt[3] > 2LL * d.L * d.L * d.L)
+            return fail(AKMC_EINVAL, "slot %d: more solutes than sites", v);
+    }
+    const Layout& lo = b->lo;
+    std::vector<int4> items;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t v = slots[i];
+        const akmc_voxel_desc& d = descs[i];
+        b->desc[v] = d;
+        VoxelDev& V = b->vox_host[v];
+        V.status = AKMC_OK;
+        species_counts(d, V.counts);
+        V.beta = 1.0 / (kKB * d.T);
+        for (int k = 0; k < 3; ++k) V.frac[k] = d.frac[k];
+        V.T = d.T;
+        V.seed = d.seed;
+        V.uid = d.uid;
+        V.n_events = 0;
+        V.t_hi = V.t_lo = 0.0;
+        V.etab_ok = 0;
+        AKMC_CUDA(cudaMemcpyAsync(b->base + lo.vox + sizeof(VoxelDev) * v, &V, sizeof V, cudaMemcpyHostToDevice, s));
+        AKMC_CUDA(cudaMemsetAsync(V.species, 0, V.N, s));
+        AKMC_CUDA(cudaMemsetAsync(V.vac_pos, 0, 4 * (size_t)V.nv, s));
+        AKMC_CUDA(cudaMemsetAsync(V.vac_disp, 0, 12 * (size_t)V.nv, s));
+        AKMC_CUDA(cudaMemsetAsync(V.rates, 0, 64 * (size_t)V.nv, s));
+        AKMC_CUDA(cudaMemsetAsync(V.dE, 0, 64 * (size_t)V.nv, s));
+        AKMC_CUDA(cudaMemsetAsync(V.hop_sp, 0, 8 * (size_t)V.nv, s));
+        AKMC_CUDA(cudaMemsetAsync(V.tree, 0, 16 * (size_t)V.P, s));
+        if (V.log) AKMC_CUDA(cudaMemsetAsync(V.log, 0, 4 * (size_t)V.log_cap, s));
+        for (const int4& it : lo.item_list)
+            if (it.x == v) items.push_back(it);
+    }
+    int32_t* list = (int32_t*)(b->base + lo.reset_list);
+    AKMC_CUDA(cudaMemcpyAsync(list, slots, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    VoxelDev* vox = (VoxelDev*)(b->base + lo.vox);
+    launch_place(vox, n, list, s);
+    AKMC_CUDA(cudaGetLastError());
+    AKMC_CUDA(launch_rate_tables(vox, n, (const ModelDev*)(b->base + lo.model), list, s));
+    BatchArgs a = b->args();
+    if (!items.empty()) {
+        AKMC_CUDA(cudaMemcpyAsync(b->base + lo.reset_items, items.data(), sizeof(int4) * items.size(),
+                                  cudaMemcpyHostToDevice, s));
+        AKMC_CUDA(launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + lo.reset_items), (int)items.size(), s));
+    }
+    AKMC_CUDA(launch_rebuild(a, 8, list, n, s));
+    // pageable sources above are staged by the copies; the tile list must outlive its copy
+    AKMC_CUDA(cudaStreamSynchronize(s));
     return AKMC_OK;
 }
 

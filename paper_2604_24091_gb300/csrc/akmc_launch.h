@@ -6,7 +6,8 @@
 namespace akmc {
 
 void launch_setup_model(ModelDev* M, int32_t* batch_status, int has_eam, int n_rho, cudaStream_t st);
-void launch_place(VoxelDev* vox, int n_vox, cudaStream_t st);
+// `list` (device, nullable): the voxel indices to work on; NULL means all.
+void launch_place(VoxelDev* vox, int n_vox, const int32_t* list, cudaStream_t st);
 cudaError_t launch_batch_load(VoxelDev* vox, const double* io, int n, int has_t, int has_n, cudaStream_t st);
 cudaError_t launch_voxel_load(VoxelDev* V, const double* io, cudaStream_t st);
 cudaError_t launch_batch_read(const VoxelDev* vox, double* io, int n, cudaStream_t st);
@@ -17,9 +18,10 @@ cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables*
                            const int4* items, int n_items, cudaStream_t st);
 
 size_t step_dyn_smem(int max_nv, int max_P);
-cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, cudaStream_t st);
+cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, const int32_t* list,
+                               cudaStream_t st);
 cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st);
-cudaError_t launch_rebuild(const BatchArgs& a, int warps, cudaStream_t st);
+cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, int n_list, cudaStream_t st);
 int step_occupancy(int warps, int max_nv, int max_P);
 
 const Tables& host_tables();   // stencil tables built on the host

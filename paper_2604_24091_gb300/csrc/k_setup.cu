@@ -105,11 +105,11 @@ __global__ void setup_model_kernel(ModelDev* M, int32_t* batch_status) {
 // of placement), Cu, Ni, Mn.  One warp per voxel evaluates 32 consecutive
 // draws at once and resolves them in draw order (a draw is taken iff its site
 // is Fe and no earlier draw of the same batch hit that site).
-__global__ void place_kernel(VoxelDev* vox, int n_vox) {
+__global__ void place_kernel(VoxelDev* vox, int n_vox, const int32_t* list) {
     const int lane = threadIdx.x & 31;
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (v >= n_vox) return;
-    VoxelDev& V = vox[v];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_vox) return;
+    VoxelDev& V = vox[list ? list[w] : w];
     const int N = V.N;
     int cnt[4];
     cnt[0] = V.nv;
@@ -238,10 +238,10 @@ void launch_setup_model(ModelDev* M, int32_t* batch_status, int has_eam, int n_r
     setup_model_kernel<<<blocks, 256, 0, st>>>(M, batch_status);
 }
 
-void launch_place(VoxelDev* vox, int n_vox, cudaStream_t st) {
+void launch_place(VoxelDev* vox, int n_vox, const int32_t* list, cudaStream_t st) {
     int threads = 128;
     int blocks = (n_vox * 32 + threads - 1) / threads;
-    place_kernel<<<blocks, threads, 0, st>>>(vox, n_vox);
+    place_kernel<<<blocks, threads, 0, st>>>(vox, n_vox, list);
 }
 
 }  // namespace akmc

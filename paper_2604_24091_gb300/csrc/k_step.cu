@@ -26,6 +26,8 @@
 // memory while it is resident.  Every result is independent of the launch
 // shape: integer sums are order-free, and the FP64 mode rates hop k in one
 // warp with a fixed lane mapping and shuffle tree.
+#include <mutex>
+
 #include "akmc_device.cuh"
 #include "akmc_launch.h"
 
@@ -746,12 +748,13 @@ __global__ void __launch_bounds__(NW * 32) step_kernel(BatchArgs a) {
 // (leaf path updates in slot order leave every node = left + right of its
 // final children).
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) rebuild_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(NW * 32) rebuild_kernel(BatchArgs a, const int32_t* list) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     __shared__ StepShared S;
     const Dyn D = carve(dyn_raw, a.max_nv, a.max_P);
+    const int vid = list ? list[blockIdx.x] : (int)blockIdx.x;
     load_model<NW>(S, a.model);
-    if (threadIdx.x == 0) S.v = a.vox[blockIdx.x];
+    if (threadIdx.x == 0) S.v = a.vox[vid];
     __syncthreads();
     if (S.v.status == kEINVAL) return;   // placement failed; uniform
     load_tables<NW>(S, a.tab, S.v.model, S.v.L == 4);
@@ -769,13 +772,13 @@ __global__ void __launch_bounds__(NW * 32) rebuild_kernel(BatchArgs a) {
     }
     if (threadIdx.x == 0 && S.numeric) S.v.status = kENUMERIC;
     __syncthreads();
-    store_voxel_state<NW>(S, D, &a.vox[blockIdx.x]);
+    store_voxel_state<NW>(S, D, &a.vox[vid]);
 }
 
 // Per-voxel rate tables (see kEtab); etab_ok = 0 if any entry over- or underflows.
-__global__ void rate_table_kernel(VoxelDev* vox, const ModelDev* M) {
+__global__ void rate_table_kernel(VoxelDev* vox, const ModelDev* M, const int32_t* list) {
     __shared__ int ok;
-    VoxelDev& V = vox[blockIdx.x];
+    VoxelDev& V = vox[list ? list[blockIdx.x] : (int)blockIdx.x];
     if (threadIdx.x == 0) ok = 1;
     __syncthreads();
     for (int i = threadIdx.x; i < kEtab; i += blockDim.x) {
@@ -799,19 +802,20 @@ static cudaError_t set_smem(const void* fn, size_t dyn) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
 }
 
-cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, cudaStream_t st) {
-    rate_table_kernel<<<n_vox, 256, 0, st>>>(vox, M);
+cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, const int32_t* list,
+                               cudaStream_t st) {
+    rate_table_kernel<<<n_vox, 256, 0, st>>>(vox, M, list);
     return cudaGetLastError();
 }
 
+// The dynamic shared-memory attribute of step_kernel<warps> must have been set
+// by step_occupancy() for this batch shape (no runtime call other than the
+// launch happens here, so the launch can be captured in a CUDA graph).
 cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st) {
     size_t dyn = step_dyn_smem(a.max_nv, a.max_P);
-    cudaError_t e = cudaSuccess;
     switch (warps) {
 #define AKMC_CASE(W)                                                              \
     case W:                                                                       \
-        e = set_smem<W>((const void*)step_kernel<W>, dyn);                        \
-        if (e != cudaSuccess) return e;                                           \
         step_kernel<W><<<grid, W * 32, dyn, st>>>(a);                             \
         break;
         AKMC_CASE(1) AKMC_CASE(2) AKMC_CASE(4) AKMC_CASE(8)
@@ -821,7 +825,9 @@ cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_rebuild(const BatchArgs& a, int warps, cudaStream_t st) {
+cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, int n_list, cudaStream_t st) {
+    const int grid = list ? n_list : a.n_vox;
+    if (grid == 0) return cudaSuccess;
     size_t dyn = step_dyn_smem(a.max_nv, a.max_P);
     cudaError_t e = cudaSuccess;
     switch (warps) {
@@ -829,7 +835,7 @@ cudaError_t launch_rebuild(const BatchArgs& a, int warps, cudaStream_t st) {
     case W:                                                                       \
         e = set_smem<W>((const void*)rebuild_kernel<W>, dyn);                     \
         if (e != cudaSuccess) return e;                                           \
-        rebuild_kernel<W><<<a.n_vox, W * 32, dyn, st>>>(a);                       \
+        rebuild_kernel<W><<<grid, W * 32, dyn, st>>>(a, list);                    \
         break;
         AKMC_CASE(1) AKMC_CASE(2) AKMC_CASE(4) AKMC_CASE(8)
 #undef AKMC_CASE
@@ -838,18 +844,33 @@ cudaError_t launch_rebuild(const BatchArgs& a, int warps, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The dynamic shared-memory attribute only ever grows (per device and kernel),
+// so a launch of one batch never runs with a limit set for a smaller one.
+static std::mutex g_attr_mu;
+static size_t g_attr_max[64][9];
+
 int step_occupancy(int warps, int max_nv, int max_P) {
-    size_t dyn = step_dyn_smem(max_nv, max_P);
+    const size_t dyn = step_dyn_smem(max_nv, max_P);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || warps < 1 || warps > 8) return 0;
+    {
+        std::lock_guard<std::mutex> lock(g_attr_mu);
+        size_t& cur = g_attr_max[dev][warps];
+        if (dyn > cur) {
+            const void* fn = warps == 1 ? (const void*)step_kernel<1> : warps == 2 ? (const void*)step_kernel<2>
+                           : warps == 4 ? (const void*)step_kernel<4> : (const void*)step_kernel<8>;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+                return 0;
+            cur = dyn;
+        }
+    }
     int n = 0;
     switch (warps) {
-        case 1: set_smem<1>((const void*)step_kernel<1>, dyn);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<1>, 32, dyn); break;
-        case 2: set_smem<2>((const void*)step_kernel<2>, dyn);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<2>, 64, dyn); break;
-        case 4: set_smem<4>((const void*)step_kernel<4>, dyn);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<4>, 128, dyn); break;
-        case 8: set_smem<8>((const void*)step_kernel<8>, dyn);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<8>, 256, dyn); break;
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<1>, 32, dyn); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<2>, 64, dyn); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<4>, 128, dyn); break;
+        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<8>, 256, dyn); break;
         default: break;
     }
     return n;
