@@ -226,7 +226,7 @@ akmc_status akmc_cluster_hist(akmc_batch* batch, int32_t voxel, int32_t mode,
 akmc_status akmc_cluster_hist_noalloc(const uint8_t* species, int32_t L, int32_t mode, int64_t* hist,
                                       akmc_stream stream);
 
-/* Launch shape of akmc_step_n: warps per voxel-CTA (1, 2, 4 or 8) and CTAs
+/* Launch shape of akmc_step_n: warps per voxel-CTA (1, 2, 4, 8 or 16) and CTAs
  * per SM (0 = as many as fit).  Results are identical for every shape. */
 akmc_status akmc_set_launch(akmc_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm);
 

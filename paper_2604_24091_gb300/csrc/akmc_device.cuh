@@ -48,6 +48,15 @@ struct Tables {
     // that the hop caused at u.  [0]: L >= 5; [1]: L = 4 (u - w taken as the
     // periodic minimal image).
     uint8_t eam_dsh[2][160][8];
+    // Prefetch region of a single vacancy at p: the union of the read sets of
+    // all 8 possible next positions p + d_k (offsets relative to p), and, per
+    // hop direction d, the region index of every union entry around p + d.
+    int32_t pair_roff[160];
+    uint16_t pair_ridx[8][64];
+    int32_t eam_roff[288];
+    uint16_t eam_ridx[8][160];
+    int32_t pair_nreg, eam_nreg;
+    int32_t pair_rc[9], eam_rc[9];   // region index of p itself ([8]) and of p + d_k ([k])
 };
 
 struct ModelDev {

@@ -145,6 +145,21 @@ Tables make_tables() {
                 int sm = contains(sph, E[u]) ? shell_of(E[u]) : 0;
                 T.eam_dsh[small][u][k] = (uint8_t)((sw << 3) | sm);
             }
+    auto region = [&](const std::vector<Off3>& Un, int32_t* roff, uint16_t* ridx, int ustride, int32_t& nreg,
+                      int32_t* rc) {
+        std::vector<Off3> R;
+        for (int k = 0; k < 8; ++k)
+            for (const Off3& u : Un) index_in(R, plus(dirs[k], u));
+        for (size_t i = 0; i < R.size(); ++i) roff[i] = off_pack(R[i].dx, R[i].dy, R[i].dz, 0);
+        for (int k = 0; k < 8; ++k)
+            for (size_t u = 0; u < Un.size(); ++u) ridx[k * ustride + u] = (uint16_t)index_in(R, plus(dirs[k], Un[u]));
+        nreg = (int32_t)R.size();
+        for (int k = 0; k < 8; ++k) rc[k] = index_in(R, dirs[k]);
+        rc[8] = index_in(R, Off3{0, 0, 0});
+        nreg = (int32_t)R.size();
+    };
+    region(U, T.pair_roff, &T.pair_ridx[0][0], 64, T.pair_nreg, T.pair_rc);
+    region(E, T.eam_roff, &T.eam_ridx[0][0], 160, T.eam_nreg, T.eam_rc);
     return T;
 }
 
@@ -358,7 +373,7 @@ struct akmc_batch {
     int stage = 0;
     bool dirty = false;
     int warps = 4, ctas_per_sm = 0, n_sm = 0, device = 0;
-    int occupancy[9] = {};             // CTAs per SM of the step kernel, by warps per CTA
+    int occupancy[17] = {};            // CTAs per SM of the step kernel, by warps per CTA
 
     BatchArgs args() const {
         BatchArgs a;
@@ -823,7 +838,8 @@ akmc_status akmc_cluster_hist(akmc_batch* b, int32_t voxel, int32_t mode, int64_
 
 akmc_status akmc_set_launch(akmc_batch* b, int32_t warps, int32_t ctas_per_sm) {
     if (!b) return fail(AKMC_EINVAL, "batch is NULL");
-    if (warps != 1 && warps != 2 && warps != 4 && warps != 8) return fail(AKMC_EINVAL, "warps must be 1,2,4,8");
+    if (warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16)
+        return fail(AKMC_EINVAL, "warps must be 1, 2, 4, 8 or 16");
     if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(AKMC_EINVAL, "ctas_per_sm out of range");
     b->warps = warps;
     b->ctas_per_sm = ctas_per_sm;

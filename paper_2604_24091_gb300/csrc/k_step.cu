@@ -53,6 +53,13 @@ struct __align__(16) StepShared {
     uint32_t ent[8][80];
     int32_t mk[8];
     uint8_t dsh[160][8];
+    // single-vacancy prefetch region (see phase_prefetch)
+    uint16_t ridx[8][160];
+    int32_t roff[288];
+    int32_t rc[9];
+    int32_t nreg;
+    uint8_t rsp[288];
+    int32_t rrho[288];
     int32_t n_rho, shift, cur_model, cur_small, vid;
     float inv_knot_f;
     VoxelDev v;
@@ -62,7 +69,7 @@ struct __align__(16) StepShared {
     int32_t srho[160];
     uint8_t ssp[160];
     uint8_t fbad[160];
-    long long acc64[8];       // split mode: dE of each hop in 2^-40 eV
+    long long acc64[2][8];    // split mode: dE of each hop in 2^-40 eV (two partial sums)
     int32_t acc32[8];         // pair model: dE of each hop in 2^-24 eV
     double hop_de[8];         // FP64 mode
     int32_t hop_bad[8];
@@ -184,12 +191,20 @@ __device__ void load_tables(StepShared& S, const Tables* T, int model, int small
         for (int i = tid; i < 64; i += NW * 32) S.off[i] = T->pair_off[i];
         for (int i = tid; i < 8 * 32; i += NW * 32) S.ent[i / 32][i % 32] = T->pair_ent[i / 32][i % 32];
         if (tid < 8) S.mk[tid] = T->pair_mk[tid];
+        for (int i = tid; i < 160; i += NW * 32) S.roff[i] = T->pair_roff[i];
+        for (int i = tid; i < 8 * 64; i += NW * 32) S.ridx[i / 64][i % 64] = T->pair_ridx[i / 64][i % 64];
+        if (tid < 9) S.rc[tid] = T->pair_rc[tid];
+        if (tid == 0) S.nreg = T->pair_nreg;
     } else {
         for (int i = tid; i < 160; i += NW * 32) S.off[i] = T->eam_off[i];
         for (int i = tid; i < 8 * 80; i += NW * 32) S.ent[i / 80][i % 80] = T->eam_ent[i / 80][i % 80];
         if (tid < 8) S.mk[tid] = T->eam_mk[tid];
         for (int i = tid; i < 64; i += NW * 32) S.sph[i] = T->sph_off[i];
         for (int i = tid; i < 160 * 8; i += NW * 32) S.dsh[i / 8][i % 8] = T->eam_dsh[small][i / 8][i % 8];
+        for (int i = tid; i < 288; i += NW * 32) S.roff[i] = T->eam_roff[i];
+        for (int i = tid; i < 8 * 160; i += NW * 32) S.ridx[i / 160][i % 160] = T->eam_ridx[i / 160][i % 160];
+        if (tid < 9) S.rc[tid] = T->eam_rc[tid];
+        if (tid == 0) S.nreg = T->eam_nreg;
     }
     __syncthreads();
     if (tid == 0) {
@@ -326,8 +341,62 @@ __device__ __forceinline__ void phase_gather(StepShared& S, const Dyn& D, int q,
             S.srho[u] = r;
         }
     }
+    if (tid < 16) S.acc64[tid >> 3][tid & 7] = 0;
     if (tid < 8) {
-        S.acc64[tid] = 0;
+        S.acc32[tid] = 0;
+        S.hop_bad[tid] = 0;
+    }
+}
+
+// Single-vacancy fast path.  phase_prefetch loads the region around the
+// vacancy's current position (the read sets of all 8 possible next
+// positions) into shared memory; it runs in the shadow of warp 0's rate
+// phase, after the event's density updates are visible.  phase_fill then
+// builds the next event's read set from that region instead of memory: the
+// swapped sites take their new species, and every density gets the hop's
+// change added.  Needs no periodic aliasing inside the region (L >= 6 for
+// EAM, L >= 5 for the pair model).
+template <int NW, int MODE>
+__device__ __forceinline__ void phase_prefetch(StepShared& S, const Dyn& D, int first_tid) {
+    constexpr int NT = NW * 32;
+    const int i0 = (int)threadIdx.x - first_tid;
+    if (i0 < 0) return;
+    const int L = S.v.L, M2 = 2 * L;
+    const int X = D.X[0], Y = D.Y[0], Z = D.Z[0];
+    for (int i = i0; i < S.nreg; i += NT - first_tid) {
+        const int o = S.roff[i];
+        const int s = site_index(wrap_coord(X + off_dx(o), M2), wrap_coord(Y + off_dy(o), M2),
+                                 wrap_coord(Z + off_dz(o), M2), L);
+        S.rsp[i] = S.v.species[s];
+        if (MODE != 0) S.rrho[i] = S.v.rho[s];
+    }
+}
+
+template <int NW, int MODE>
+__device__ __forceinline__ void phase_fill(StepShared& S) {
+    constexpr int NT = NW * 32;
+    constexpr int U = MODE != 0 ? kEamU : kPairU;
+    const int tid = threadIdx.x;
+    const int d = S.dir, A = S.A;
+    const int rc_old = S.rc[8], rc_new = S.rc[d];
+    if (tid == NT - 1) next_uniforms(S);   // the next event's Philox block
+    for (int u = tid; u < U; u += NT) {
+        const int ri = S.ridx[d][u];
+        const int sp = ri == rc_old ? A : (ri == rc_new ? kVac : S.rsp[ri]);
+        S.ssp[u] = (uint8_t)sp;
+        if (MODE != 0) {
+            const int ds = S.dsh[u][d];
+            const int r = S.rrho[ri] + S.fq[A][ds >> 3] - S.fq[A][ds & 7];
+            S.srho[u] = r;
+            if (MODE == 1) {
+                int bad = 0;
+                S.fsite[u] = sp == kVac ? 0 : embed_q(S, sp, r, bad);
+                S.fbad[u] = (uint8_t)bad;
+            }
+        }
+    }
+    if (tid < 16) S.acc64[tid >> 3][tid & 7] = 0;
+    if (tid < 8) {
         S.acc32[tid] = 0;
         S.hop_bad[tid] = 0;
     }
@@ -362,13 +431,16 @@ __device__ __forceinline__ void phase_terms(StepShared& S, bool moved) {
         }
     } else if (MODE == 1) {
         // (a3) dE = sum_i [F(rho_i + drho_i) - F(rho_i)] + own term + pair terms,
-        // every term an integer in 2^-40 eV; one warp per hop, integer shuffle sum.
-        for (int k = warp; k < 8; k += NW) {
+        // every term an integer in 2^-40 eV; one (or two) warps per hop, integer
+        // shuffle sums.
+        constexpr int WPH = NW >= 16 ? 2 : 1;
+        for (int kk = warp; kk < 8 * WPH; kk += NW) {
+            const int k = kk & 7, half = kk >> 3;
             const int A = S.ssp[S.mk[k]];
             if (A == kVac) continue;
             long long v = 0;
             int bad = 0;
-            for (int e = lane; e < kEamE; e += 32) {
+            for (int e = half * 32 + lane; e < kEamE; e += 32 * WPH) {
                 const uint32_t en = S.ent[k][e];
                 if (en >> 14) {
                     const int mk = S.mk[k];
@@ -387,8 +459,8 @@ __device__ __forceinline__ void phase_terms(StepShared& S, bool moved) {
             v = warp_sum(v);
             bad = __any_sync(0xffffffffu, bad);
             if (lane == 0) {
-                S.acc64[k] = v;
-                S.hop_bad[k] = bad;
+                S.acc64[half][k] = v;
+                if (bad) S.hop_bad[k] = 1;
             }
         }
     } else {
@@ -457,7 +529,8 @@ __device__ __forceinline__ void phase_rates(StepShared& S, const Dyn& D, int q) 
             de = S.hop_de[lane];
             g = hop_rate_fp64(S, D, A, de);
         } else {
-            const int dq = MODE == 0 ? S.acc32[lane] : (int)((S.acc64[lane] + (1LL << 15)) >> 16);
+            const int dq = MODE == 0 ? S.acc32[lane]
+                                     : (int)((S.acc64[0][lane] + S.acc64[1][lane] + (1LL << 15)) >> 16);
             de = A == kVac ? 0.0 : (double)dq * 0x1p-24;
             g = hop_rate_grid(S, D, A, dq);
         }
@@ -669,31 +742,43 @@ __device__ void run_events(StepShared& S, const Dyn& D, uint64_t target) {
     const int L = S.v.L, M2 = 2 * L;
     constexpr int reach = MODE != 0 ? 8 : 4;
     int ccount = S.ccount;   // uniform copy of the clock-batch fill
+    const bool fast = S.v.nv == 1 && L >= (MODE != 0 ? 6 : 5);
+    if (fast) {
+        phase_prefetch<NW, MODE>(S, D, 0);
+        __syncthreads();
+    }
     for (uint64_t done = 0; done < target; ++done) {
         if (tid == 0) S.stop = !select_and_swap(S, D);
         __syncthreads();
         if (S.stop) break;
         ++ccount;
-        // (a8) other vacancies whose read set may contain a changed site: every
-        // vacancy within `reach` half units of w per axis.
-        for (int q = tid; q < S.v.nv; q += NW * 32) {
-            if (q == S.slot) continue;
-            int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
-            ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
-            ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
-            ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
-            if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach) D.aff[atomicAdd(&S.n_aff, 1)] = q;
-        }
-        phase_gather<NW, MODE>(S, D, S.slot, true);
-        __syncthreads();
-        if (MODE == 1) {
-            phase_site_embed<NW>(S);
+        if (fast) {
+            phase_fill<NW, MODE>(S);
             __syncthreads();
+        } else {
+            // (a8) other vacancies whose read set may contain a changed site: every
+            // vacancy within `reach` half units of w per axis.
+            for (int q = tid; q < S.v.nv; q += NW * 32) {
+                if (q == S.slot) continue;
+                int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
+                ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
+                ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
+                ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
+                if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach)
+                    D.aff[atomicAdd(&S.n_aff, 1)] = q;
+            }
+            phase_gather<NW, MODE>(S, D, S.slot, true);
+            __syncthreads();
+            if (MODE == 1) {
+                phase_site_embed<NW>(S);
+                __syncthreads();
+            }
         }
         phase_terms<NW, MODE>(S, true);
         __syncthreads();
         if (tid < 32) phase_rates<MODE>(S, D, S.slot);
-        const int n_aff = S.n_aff;
+        if (fast) phase_prefetch<NW, MODE>(S, D, NW > 1 ? 32 : 0);
+        const int n_aff = fast ? 0 : S.n_aff;
         if (n_aff > 0) {
             __syncthreads();
             for (int i = 0; i < n_aff; ++i) refresh_full<NW, MODE>(S, D, D.aff[i]);
@@ -818,7 +903,7 @@ cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st
     case W:                                                                       \
         step_kernel<W><<<grid, W * 32, dyn, st>>>(a);                             \
         break;
-        AKMC_CASE(1) AKMC_CASE(2) AKMC_CASE(4) AKMC_CASE(8)
+        AKMC_CASE(1) AKMC_CASE(2) AKMC_CASE(4) AKMC_CASE(8) AKMC_CASE(16)
 #undef AKMC_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -837,7 +922,7 @@ cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, i
         if (e != cudaSuccess) return e;                                           \
         rebuild_kernel<W><<<grid, W * 32, dyn, st>>>(a, list);                    \
         break;
-        AKMC_CASE(1) AKMC_CASE(2) AKMC_CASE(4) AKMC_CASE(8)
+        AKMC_CASE(1) AKMC_CASE(2) AKMC_CASE(4) AKMC_CASE(8) AKMC_CASE(16)
 #undef AKMC_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -847,19 +932,20 @@ cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, i
 // The dynamic shared-memory attribute only ever grows (per device and kernel),
 // so a launch of one batch never runs with a limit set for a smaller one.
 static std::mutex g_attr_mu;
-static size_t g_attr_max[64][9];
+static size_t g_attr_max[64][17];
 
 int step_occupancy(int warps, int max_nv, int max_P) {
     const size_t dyn = step_dyn_smem(max_nv, max_P);
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || warps < 1 || warps > 8) return 0;
+    if (dev < 0 || dev >= 64 || warps < 1 || warps > 16) return 0;
     {
         std::lock_guard<std::mutex> lock(g_attr_mu);
         size_t& cur = g_attr_max[dev][warps];
         if (dyn > cur) {
             const void* fn = warps == 1 ? (const void*)step_kernel<1> : warps == 2 ? (const void*)step_kernel<2>
-                           : warps == 4 ? (const void*)step_kernel<4> : (const void*)step_kernel<8>;
+                           : warps == 4 ? (const void*)step_kernel<4> : warps == 8 ? (const void*)step_kernel<8>
+                           : (const void*)step_kernel<16>;
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
                 return 0;
             cur = dyn;
@@ -871,6 +957,7 @@ int step_occupancy(int warps, int max_nv, int max_P) {
         case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<2>, 64, dyn); break;
         case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<4>, 128, dyn); break;
         case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<8>, 256, dyn); break;
+        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<16>, 512, dyn); break;
         default: break;
     }
     return n;

@@ -67,7 +67,7 @@ def test_placement_and_initial_rates(model):
             _assert_rates(g["rates"], o["rates"], rtol=1e-3)
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16])
 def test_pair_trajectory_bit_exact(model, warps):
     # plain configuration (16^3 cells, Fe-1.34Cu, 1 vacancy) and a dense
     # multi-vacancy lattice, stepped in two chunks
@@ -145,7 +145,7 @@ def test_batch_and_launch_shape_invariance(model):
         b.step(n)
         alone.append(b.read_state(0, log=True))
         b.close()
-    for warps in (1, 8):
+    for warps in (1, 8, 16):
         b = Batch(descs, model, event_log_capacity=n)
         b.set_launch(warps, 1)
         b.step(n)
@@ -270,3 +270,29 @@ def test_batch_state_roundtrip_and_validation(model):
     c.step(10)
     st, per = c.sync_status()
     assert per[0] == 1 and (per[1:] == 0).all()
+
+
+def test_single_vacancy_fast_path_matches_oracle(model):
+    # one vacancy and L >= 6 (EAM) / L >= 5 (pair) take the prefetched-region
+    # path; the trajectories must still match the oracle event by event
+    descs = [synth.VoxelDesc(6, 1, (0.12, 0.10, 0.08), 563.0, synth.EAM_MODEL, synth.PREC_FP64, seed=81, uid=9),
+             synth.VoxelDesc(7, 1, (0.10, 0.08, 0.08), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT, seed=82, uid=10),
+             synth.VoxelDesc(5, 1, (0.15, 0.10, 0.10), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=83, uid=11)]
+    n = 4000
+    for warps in (1, 8, 16):
+        b = Batch(descs, model, event_log_capacity=n)
+        b.set_launch(warps, 0)
+        b.step(n // 2)
+        b.step(n // 2)
+        for v, d in enumerate(descs):
+            g = b.read_state(v, log=True)
+            o = oracle.Voxel(d, model)
+            log_o = o.step(n, log=True)
+            so = o.state()
+            if d.precision == synth.PREC_FP64:
+                assert np.array_equal(g["event_log"], log_o)
+                assert np.array_equal(g["species"], so["species"])
+                _assert_rates(g["rates"], so["rates"])
+            o2 = oracle.Voxel(d, model)
+            o2.load(g["species"], g["vac_pos"])
+            assert np.abs(g["dE"] - o2.state()["dE"]).max() <= (1e-12 if d.precision == 0 else SPLIT_DE_TOL)
