@@ -146,6 +146,11 @@ def cpu_oracle_rate(descs, events_per_voxel, procs):
     return ev / wall, ev, wall
 
 
+def workload_name(events_per_voxel):
+    return ("batched EAM: %d voxels x 32^3 cells (65536 sites), Fe-0.3Cu-0.7Ni-1.4Mn at%%, 1 vacancy, 563 K, "
+            "%d events per voxel per step" % (N_VOX, events_per_voxel))
+
+
 def reference_arm(args):
     """--impl reference: the oracle timed on the host cores, same metric and
     workload, each step a bounded sample (one voxel per core, fixed events)."""
@@ -155,8 +160,8 @@ def reference_arm(args):
     procs = os.cpu_count() or 1
     descs = synth.config_batched_eam(N_VOX)
     per = args.ref_events
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_oracle_rate(descs, max(200, per // 10), procs)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(descs, max(200, per // 50), procs)
     rates, walls, evs = [], [], 0
     for _ in range(args.steps):
         r, ev, wall = cpu_oracle_rate(descs, per, procs)
@@ -169,8 +174,8 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "batched EAM 256 x 32^3 cells, Fe-0.3Cu-0.7Ni-1.4Mn, 1 vacancy, 563 K",
-                       "sample": sample},
+            "config": {"workload": workload_name(args.events), "voxels_per_gpu": N_VOX,
+                       "events_per_voxel_per_step": int(args.events), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -194,9 +199,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--events", type=int, default=1_000_000, help="events per voxel per step")
-    ap.add_argument("--ref-events", type=int, default=20000, help="oracle events per core per step")
+    ap.add_argument("--ref-events", type=int, default=100000,
+                    help="oracle events per host core per step (reference arm; the cpu_baseline leg runs 3x)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/rate-kernel/cpu legs")
     ap.add_argument("--launch", default=None, help="warps,ctas_per_sm of the step kernel (skips the tuner)")
+    ap.add_argument("--rate-kernel", action="store_true",
+                    help="run only the rate-kernel leg (300 EAM voxels of 64^3 cells) and print its JSON")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload (Poisson arrivals, continuous batching) instead")
     args = ap.parse_args()
@@ -204,6 +212,13 @@ def main():
         return reference_arm(args)
     if args.serving:
         return serving(args)
+    if args.rate_kernel:
+        import torch
+        from paper_2604_24091_gb300 import Batch
+        torch.cuda.set_device(0)
+        peak, peak_kind = _peaks()
+        print(json.dumps(rate_kernel_leg(synth.default_model(), torch, peak, peak_kind, Batch)), flush=True)
+        return
 
     import torch
     import torch.distributed as dist
@@ -266,15 +281,14 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (EAM split: FP32 embedding, exact "
         "fixed-point + FP64 assembly, FP64 rate sums and clock)", "data": "synthetic",
-        "config": {"workload": "batched EAM: %d voxels x 32^3 cells (65536 sites), Fe-0.3Cu-0.7Ni-1.4Mn at%%, "
-                   "1 vacancy, 563 K, %d events per voxel per step" % (N_VOX, E),
+        "config": {"workload": workload_name(E),
                    "voxels_per_gpu": N_VOX, "events_per_voxel_per_step": E, "launch": [warps, per_sm],
                    "l2": "flushed between timed steps (256 MB write)", "wall_s_timed_region": t_wall},
         "roofline": {"bound": "hbm", "kernel": "step_kernel (persistent, one CTA per voxel)",
                      "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "bytes_per_event": EAM_BYTES_PER_EVENT,
-                     "note": "latency-bound: each voxel is one serial event chain; see DESIGN.md"},
+                     "note": "latency-bound: each voxel is one serial event chain"},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -284,6 +298,25 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def rate_kernel_leg(model, torch, peak, peak_kind, Batch):
+    """akmc_compute_rates (densities + rates + trees) over a working set
+    larger than L2: 300 EAM voxels of 64^3 cells (157 M sites: 157 MB species
+    + 629 MB densities).  Best of 5 launches."""
+    big = [synth.VoxelDesc(64, 2, (0.002, 0.01, 0.01), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT,
+                           synth.splitmix64(99, u), u) for u in range(300)]
+    rb = Batch(big, model)
+    rb.compute_rates()
+    ts = [_time_region(rb.compute_rates, torch) for _ in range(5)]
+    sites = sum(2 * d.L ** 3 for d in big)
+    gbs = RATE_BYTES_PER_SITE * sites / min(ts) / 1e9
+    rb.close()
+    return {"bound": "hbm", "kernel": "akmc_compute_rates (density + rates + trees)",
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": None, "peak_kind": peak_kind,
+            "workload": "300 EAM voxels x 64^3 cells, 157 M sites (> L2)",
+            "ms": 1e3 * min(ts)}
 
 
 def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
@@ -323,24 +356,10 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
                     "config": "Fe-1.34Cu 16^3 cells pair model FP64, 1 voxel, one kernel launch per event",
                     "persistent_one_voxel": n_pers / tp}
     p.close()
-    # rate kernel over a working set larger than L2: 300 EAM voxels of 64^3
-    # cells (157 M sites: 157 MB species + 629 MB densities)
-    big = [synth.VoxelDesc(64, 2, (0.002, 0.01, 0.01), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT,
-                           synth.splitmix64(99, u), u) for u in range(300)]
-    rb = Batch(big, model)
-    rb.compute_rates()
-    ts = [_time_region(rb.compute_rates, torch) for _ in range(5)]
-    sites = sum(2 * d.L ** 3 for d in big)
-    gbs = RATE_BYTES_PER_SITE * sites / min(ts) / 1e9
-    out["rate_kernel_roofline"] = {"bound": "hbm", "kernel": "akmc_compute_rates (density + rates + trees)",
-                                   "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                                   "traffic": None, "peak_kind": peak_kind,
-                                   "workload": "300 EAM voxels x 64^3 cells, 157 M sites (> L2)",
-                                   "ms": 1e3 * min(ts)}
-    rb.close()
+    out["rate_kernel_roofline"] = rate_kernel_leg(model, torch, peak, peak_kind, Batch)
     # the oracle on the host cores, bounded sample of the same workload
     procs = os.cpu_count() or 1
-    per = args.ref_events
+    per = 3 * args.ref_events
     r, ev, wall = cpu_oracle_rate(descs, per, procs)
     out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
                            "sample": "%d voxels of the workload, one per host core, %d events each (%.1f s)"

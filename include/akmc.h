@@ -164,6 +164,16 @@ akmc_status akmc_reset_voxels(akmc_batch* batch, const int32_t* slots, const akm
 /* Copy one voxel's state to host memory; synchronises the stream. */
 akmc_status akmc_read_state(akmc_batch* batch, int32_t voxel, akmc_state* out, akmc_stream stream);
 
+/* Copy the EAM site densities of one voxel to host memory: rho[s] for every
+ * site s (2L^3 int32, site order as above), in fixed point with unit 2^-24
+ * (rho_s = sum over the 58 sites j within the cutoff, j not a vacancy, of
+ * f_{sigma_j}(r_sj), each term rounded to that unit: the density that enters
+ * the EAM embedding energy).  host_rho is caller-owned.  Fails with
+ * AKMC_EINVAL for a pair-model voxel, a NULL pointer, or while the batch's
+ * densities are out of date after a state load (call akmc_compute_rates
+ * first).  Synchronises the stream. */
+akmc_status akmc_read_density(akmc_batch* batch, int32_t voxel, int32_t* host_rho, akmc_stream stream);
+
 /* Replace one voxel's lattice (same L and n_vac), clock and event counter;
  * displacements restart at 0.  The next akmc_step_n or akmc_compute_rates
  * rebuilds rates first.  Host inputs are copied before return. */

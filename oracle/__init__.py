@@ -74,6 +74,7 @@ def lib():
                 "orc_hop_de_brute": (D, [P, I, I]),
                 "orc_hop_rate": (D, [P, I, I]),
                 "orc_rho_fixed": (ctypes.c_int64, [P, I]),
+                "orc_rho_all": (None, [P, P]),
                 "orc_set_debug": (None, [P, I]),
                 "orc_debug_counts": (None, [P, P]),
                 "orc_tracer_r2": (D, [P]),
@@ -199,6 +200,11 @@ class Voxel:
     def rho_fixed(self, site):
         return int(self._lib.orc_rho_fixed(self._h, int(site)))
 
+    def rho_all(self):
+        out = np.zeros(self.n_sites, np.int64)
+        self._lib.orc_rho_all(self._h, _ptr(out))
+        return out
+
     def set_debug(self, flags):
         self._lib.orc_set_debug(self._h, int(flags))
 
@@ -247,3 +253,33 @@ def event_uniforms(seed, uid, n):
     u1, u2 = ctypes.c_double(), ctypes.c_double()
     lib().orc_event_uniforms(int(seed), int(uid), int(n), ctypes.byref(u1), ctypes.byref(u2))
     return u1.value, u2.value
+
+
+def _ensemble_worker(args):
+    desc, model, n_events, mode, start = args
+    v = Voxel(desc, model)
+    if start is not None:
+        v.load(*start)
+    h0 = v.cluster_hist(mode)[0]
+    v.step(n_events)
+    return h0, v.cluster_hist(mode)[0], int(v.status)
+
+
+def ensemble_cluster_hist(descs, model, n_events, mode=0, procs=None, start=None):
+    """Cu cluster histograms of independent oracle runs: each voxel starts from
+    its seeded placement (or from `start` = (species, vac_pos), the same
+    lattice for every voxel) and takes `n_events` events.  Returns (initial
+    histograms, final histograms, statuses), one row per voxel.  Voxels run on
+    `procs` spawned processes (never forked, so callers that already hold a
+    CUDA context are safe)."""
+    import multiprocessing as mp
+    build()
+    procs = max(1, min(len(descs), procs or os.cpu_count() or 1))
+    jobs = [(d, model, int(n_events), int(mode), start) for d in descs]
+    if procs == 1:
+        res = [_ensemble_worker(j) for j in jobs]
+    else:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_ensemble_worker, jobs)
+    return (np.array([r[0] for r in res]), np.array([r[1] for r in res]),
+            np.array([r[2] for r in res]))

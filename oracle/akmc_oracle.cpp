@@ -766,6 +766,10 @@ double orc_hop_rate(const orc_voxel* v, int slot, int dir) {
 
 int64_t orc_rho_fixed(const orc_voxel* v, int site) { return rho_scratch(v, v->sp.data(), site); }
 
+void orc_rho_all(const orc_voxel* v, int64_t* out) {
+    for (int i = 0; i < v->N; ++i) out[i] = rho_scratch(v, v->sp.data(), i);
+}
+
 void orc_set_debug(orc_voxel* v, int flags) { v->debug = flags; }
 
 void orc_debug_counts(const orc_voxel* v, uint64_t out[5]) {

@@ -75,6 +75,8 @@ double orc_hop_de_brute(const orc_voxel* v, int slot, int dir);
 double orc_hop_rate(const orc_voxel* v, int slot, int dir);
 /* Site density rho_i (fixed point, units 2^-24) recomputed from scratch. */
 int64_t orc_rho_fixed(const orc_voxel* v, int site);
+/* rho_fixed of every site (N entries), from the current lattice. */
+void orc_rho_all(const orc_voxel* v, int64_t* out);
 
 /* Debug checks: 1 incremental rates == scratch rates every event,
  * 2 tree selection == linear cumulative scan, 4 stored rho == scratch rho,

@@ -76,6 +76,7 @@ def load_library():
             "akmc_batch_sites": (SZ, [P]),
             "akmc_batch_vacancies": (ctypes.c_int64, [P]),
             "akmc_cluster_hist": (I32, [P, I32, I32, P, P]),
+            "akmc_read_density": (I32, [P, I32, P, P]),
             "akmc_cluster_hist_noalloc": (I32, [P, I32, I32, P, P]),
             "akmc_set_launch": (I32, [P, I32, I32]),
             "akmc_n_voxels": (I32, [P]),
@@ -323,6 +324,13 @@ class Batch:
         if st == ECUDA:
             _check(st)
         return int(st), per
+
+    def read_density(self, voxel, stream=None):
+        """EAM site densities of one voxel (int32, unit 2^-24), site order."""
+        L = self.descs[voxel].L
+        rho = np.zeros(2 * L ** 3, np.int32)
+        _check(self._lib.akmc_read_density(self._h, int(voxel), _ptr(rho), _stream_ptr(stream)))
+        return rho
 
     def cluster_hist(self, voxel, mode=0, stream=None):
         h = np.zeros(8, np.int64)

@@ -121,7 +121,18 @@ struct BatchArgs {
     int32_t* batch_status;     // batch-level error word
     int32_t n_vox;
     int32_t max_nv, max_P;
+    int32_t win;               // edge (cells) of the shared-memory lattice window, 0 = none
 };
+
+// Edge (cells) of the shared-memory lattice window of a single-vacancy voxel.
+// The window path steps single-vacancy voxels of the pair model or of EAM in
+// split precision with L >= 5 (the stencils of the vacancy and of its 8
+// targets fit in a window of min(L, 16) cells with no periodic self-aliasing).
+constexpr int kWinMax = 16;
+__host__ __device__ inline int window_edge(int L, int n_vac, int model, int precision) {
+    if (n_vac != 1 || L < 5 || (model != 0 && precision != 1)) return 0;
+    return L < kWinMax ? L : kWinMax;
+}
 
 // ---------------------------------------------------------------- helpers
 

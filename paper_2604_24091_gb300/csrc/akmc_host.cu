@@ -267,8 +267,11 @@ struct Layout {
     std::vector<size_t> species, rho, pos, disp, rates, dE, hop, tree, log, etab;
     size_t state_begin = 0, state_end = 0, io = 0, reset_list = 0, reset_items = 0;
     size_t b_species = 0, b_pos = 0, b_disp = 0, tot_N = 0, tot_nv = 0;
-    std::vector<int4> item_list;
-    int max_nv = 1, max_P = 1;
+    std::vector<int4> item_list;       // density tiles (voxels with L > kStripMaxL)
+    std::vector<int4> strip_list;      // density strips (voxels with L <= kStripMaxL)
+    size_t strips = 0, reset_strips = 0;
+    int strip_ty = 16, strip_lmax = 0;
+    int max_nv = 1, max_P = 1, win = 0;
     size_t max_N = 0;
     bool has_eam = false;
 };
@@ -296,12 +299,46 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         for (int32_t v = 0; v < n; ++v) {
             if (d[v].model != AKMC_EAM) continue;
             int L = d[v].L;
+            if (L <= kStripMaxL) {
+                Lo.strip_lmax = std::max(Lo.strip_lmax, L);
+                continue;
+            }
             for (int z = 0; z < L; z += kTZ)
                 for (int y = 0; y < L; y += kTY)
                     for (int x = 0; x < L; x += kTX) Lo.item_list.push_back(make_int4(v, x, y, z));
         }
+        // Strips: ty rows per strip (bounded by shared memory and by one 16-byte
+        // chunk of the haloed strip per thread); the z extent tz is the largest
+        // of {L, 64, 32, 16, 8} that still gives >= 1024 strips (several waves).
+        if (Lo.strip_lmax > 0) {
+            const int lm = Lo.strip_lmax;
+            Lo.strip_ty = lm <= 64 ? 16 : (lm <= 128 ? 8 : 4);
+            const int cand[5] = {1 << 30, 64, 32, 16, 8};
+            int tz_cap = 8;
+            for (int ci = 0; ci < 5; ++ci) {
+                long long cnt = 0;
+                for (int32_t v = 0; v < n; ++v) {
+                    if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL) continue;
+                    const int L = d[v].L, tz = std::min(cand[ci], L);
+                    cnt += (long long)((L + Lo.strip_ty - 1) / Lo.strip_ty) * ((L + tz - 1) / tz);
+                }
+                if (cnt >= 1024) {
+                    tz_cap = cand[ci];
+                    break;
+                }
+            }
+            for (int32_t v = 0; v < n; ++v) {
+                if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL) continue;
+                const int L = d[v].L, tz = std::min(tz_cap, L);
+                for (int z = 0; z < L; z += tz)
+                    for (int y = 0; y < L; y += Lo.strip_ty)
+                        Lo.strip_list.push_back(make_int4(v, y, z, std::min(tz, L - z)));
+            }
+        }
         Lo.items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
         Lo.reset_items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
+        Lo.strips = take(sizeof(int4) * std::max<size_t>(1, Lo.strip_list.size()));
+        Lo.reset_strips = take(sizeof(int4) * std::max<size_t>(1, Lo.strip_list.size()));
     }
     Lo.reset_list = take(sizeof(int32_t) * n);
     Lo.io = take(32 * (size_t)n);
@@ -314,6 +351,7 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         int nv = d[v].n_vac, P = next_pow2(nv);
         Lo.max_nv = std::max(Lo.max_nv, nv);
         Lo.max_P = std::max(Lo.max_P, P);
+        Lo.win = std::max(Lo.win, window_edge(d[v].L, nv, d[v].model, d[v].precision));
         Lo.max_N = std::max(Lo.max_N, N);
         Lo.species.push_back(tot_N);
         Lo.rho.push_back(d[v].model == AKMC_EAM ? tot_rho : 0);
@@ -347,6 +385,14 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         Lo.tree[v] = b_tree + sizeof(double) * Lo.tree[v];
         Lo.log.push_back(log_cap > 0 ? b_log + sizeof(int32_t) * (size_t)log_cap * v : 0);
         Lo.etab.push_back(b_etab + sizeof(double) * kEtab * (size_t)v);
+    }
+    // 16-byte rows (vector loads and stores) where L % 8 == 0 and both
+    // arrays of the voxel start on a 16-byte boundary of the 256-byte aligned
+    // workspace.
+    for (int4& it : Lo.strip_list) {
+        const int v = it.x, L = d[v].L;
+        const bool vec = L % 8 == 0 && Lo.species[v] % 16 == 0 && Lo.rho[v] % 16 == 0;
+        it.w |= (vec ? 1 : 0) << 16;
     }
     Lo.state_end = o;
     Lo.labels = take(sizeof(int32_t) * Lo.max_N);
@@ -387,6 +433,7 @@ struct akmc_batch {
         a.n_vox = n;
         a.max_nv = lo.max_nv;
         a.max_P = lo.max_P;
+        a.win = lo.win;
         return a;
     }
 };
@@ -395,9 +442,10 @@ namespace {
 
 akmc_status rebuild(akmc_batch* b, cudaStream_t st) {
     BatchArgs a = b->args();
-    if (b->lo.has_eam && !b->lo.item_list.empty()) {
+    if (b->lo.has_eam && (!b->lo.item_list.empty() || !b->lo.strip_list.empty())) {
         cudaError_t e = launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + b->lo.items),
-                                       (int)b->lo.item_list.size(), st);
+                                       (int)b->lo.item_list.size(), (const int4*)(b->base + b->lo.strips),
+                                       (int)b->lo.strip_list.size(), b->lo.strip_ty, b->lo.strip_lmax, st);
         if (e != cudaSuccess) return fail(AKMC_ECUDA, "density kernel: %s", cudaGetErrorString(e));
     }
     cudaError_t e = launch_rebuild(a, 8, nullptr, 0, st);
@@ -544,6 +592,9 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
         if (!lo.item_list.empty())
             AKMC_TRY(cudaMemcpyAsync(b->base + lo.items, lo.item_list.data(), sizeof(int4) * lo.item_list.size(),
                                      cudaMemcpyHostToDevice, s));
+        if (!lo.strip_list.empty())
+            AKMC_TRY(cudaMemcpyAsync(b->base + lo.strips, lo.strip_list.data(),
+                                     sizeof(int4) * lo.strip_list.size(), cudaMemcpyHostToDevice, s));
     }
     AKMC_TRY(cudaMemsetAsync(b->base + lo.state_begin, 0, lo.state_end - lo.state_begin, s));
     launch_setup_model((ModelDev*)(b->base + lo.model), (int32_t*)(b->base + lo.status), has_eam,
@@ -591,7 +642,7 @@ akmc_status akmc_set_targets(akmc_batch* b, const uint64_t* n_events, akmc_strea
                               cudaMemcpyHostToDevice, s));
     AKMC_CUDA(cudaEventRecord(b->staging_done[slot], s));
     b->staging_used[slot] = true;
-    if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P);
+    if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P, b->lo.win);
     return AKMC_OK;
 }
 
@@ -599,7 +650,7 @@ akmc_status akmc_launch_step(akmc_batch* b, akmc_stream stream) {
     if (!b) return fail(AKMC_EINVAL, "batch is NULL");
     if (b->dirty) return fail(AKMC_EINVAL, "rates are out of date after a state load: call akmc_compute_rates");
     cudaStream_t s = (cudaStream_t)stream;
-    if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P);
+    if (b->occupancy[b->warps] == 0) b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P, b->lo.win);
     AKMC_CUDA(cudaMemsetAsync(b->base + b->lo.queue, 0, sizeof(uint32_t), s));
     int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy[b->warps];
     if (per_sm < 1) per_sm = 1;
@@ -645,7 +696,7 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
             return fail(AKMC_EINVAL, "slot %d: more solutes than sites", v);
     }
     const Layout& lo = b->lo;
-    std::vector<int4> items;
+    std::vector<int4> items, strips;
     for (int32_t i = 0; i < n; ++i) {
         const int32_t v = slots[i];
         const akmc_voxel_desc& d = descs[i];
@@ -672,6 +723,8 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
         if (V.log) AKMC_CUDA(cudaMemsetAsync(V.log, 0, 4 * (size_t)V.log_cap, s));
         for (const int4& it : lo.item_list)
             if (it.x == v) items.push_back(it);
+        for (const int4& it : lo.strip_list)
+            if (it.x == v) strips.push_back(it);
     }
     int32_t* list = (int32_t*)(b->base + lo.reset_list);
     AKMC_CUDA(cudaMemcpyAsync(list, slots, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
@@ -680,11 +733,16 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
     AKMC_CUDA(cudaGetLastError());
     AKMC_CUDA(launch_rate_tables(vox, n, (const ModelDev*)(b->base + lo.model), list, s));
     BatchArgs a = b->args();
-    if (!items.empty()) {
+    if (!items.empty())
         AKMC_CUDA(cudaMemcpyAsync(b->base + lo.reset_items, items.data(), sizeof(int4) * items.size(),
                                   cudaMemcpyHostToDevice, s));
-        AKMC_CUDA(launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + lo.reset_items), (int)items.size(), s));
-    }
+    if (!strips.empty())
+        AKMC_CUDA(cudaMemcpyAsync(b->base + lo.reset_strips, strips.data(), sizeof(int4) * strips.size(),
+                                  cudaMemcpyHostToDevice, s));
+    if (!items.empty() || !strips.empty())
+        AKMC_CUDA(launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + lo.reset_items), (int)items.size(),
+                                 (const int4*)(b->base + lo.reset_strips), (int)strips.size(), lo.strip_ty,
+                                 lo.strip_lmax, s));
     AKMC_CUDA(launch_rebuild(a, 8, list, n, s));
     // pageable sources above are staged by the copies; the tile list must outlive its copy
     AKMC_CUDA(cudaStreamSynchronize(s));
@@ -716,6 +774,18 @@ akmc_status akmc_read_state(akmc_batch* b, int32_t voxel, akmc_state* out, akmc_
     out->status = cur.status;
     out->L = H.L;
     out->n_vac = H.nv;
+    return AKMC_OK;
+}
+
+akmc_status akmc_read_density(akmc_batch* b, int32_t voxel, int32_t* host_rho, akmc_stream stream) {
+    if (!b || !host_rho) return fail(AKMC_EINVAL, "batch or host_rho is NULL");
+    if (voxel < 0 || voxel >= b->n) return fail(AKMC_EINVAL, "voxel %d out of range", voxel);
+    const VoxelDev& H = b->vox_host[voxel];
+    if (!H.rho) return fail(AKMC_EINVAL, "voxel %d uses the pair model (no densities)", voxel);
+    if (b->dirty) return fail(AKMC_EINVAL, "densities are out of date after a state load; call akmc_compute_rates");
+    cudaStream_t s = (cudaStream_t)stream;
+    AKMC_CUDA(cudaMemcpyAsync(host_rho, H.rho, sizeof(int32_t) * (size_t)H.N, cudaMemcpyDeviceToHost, s));
+    AKMC_CUDA(cudaStreamSynchronize(s));
     return AKMC_OK;
 }
 

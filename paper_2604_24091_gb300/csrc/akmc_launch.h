@@ -14,15 +14,19 @@ cudaError_t launch_batch_read(const VoxelDev* vox, double* io, int n, cudaStream
 
 // Density tiles: cells [x0,x0+kTX) x [y0,y0+kTY) x [z0,z0+kTZ) of one voxel.
 constexpr int kTX = 32, kTY = 16, kTZ = 16, kHalo = 2;
-cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab,
-                           const int4* items, int n_items, cudaStream_t st);
+// Strips (voxels with L <= kStripMaxL): item (voxel, y0, z0, tz | vec << 16)
+// covers rows [y0, y0+ty) of planes [z0, z0+tz); vec = 16-byte aligned rows.
+constexpr int kStripMaxL = 256;
+cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
+                           int n_tiles, const int4* strips, int n_strips, int strip_ty, int strip_lmax,
+                           cudaStream_t st);
 
-size_t step_dyn_smem(int max_nv, int max_P);
+size_t step_dyn_smem(int max_nv, int max_P, int win);
 cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, const int32_t* list,
                                cudaStream_t st);
 cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st);
 cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, int n_list, cudaStream_t st);
-int step_occupancy(int warps, int max_nv, int max_P);
+int step_occupancy(int warps, int max_nv, int max_P, int win);
 
 const Tables& host_tables();   // stencil tables built on the host
 void set_last_error(const char* msg);   // text returned by akmc_last_error() on this thread

@@ -83,6 +83,14 @@ struct __align__(16) StepShared {
     int32_t stop, numeric, n_aff;
     int32_t slot, dir, A;
     int32_t wX, wY, wZ, mX, mY, mZ;
+    // single-vacancy lattice window (see run_events_window)
+    int32_t W, ox, oy, oz;            // edge and origin (cells) of the window
+    int32_t lX, lY, lZ, wb;           // vacancy: local half-unit coordinates, window index
+    int32_t recenter;
+    int32_t hsp[8], hbad[2][8];       // hop atoms and range flags from the terms phase
+    int32_t pA, pw, pm, pwb, pmb;     // hop whose density change is pending: atom, window sites, parities
+    int32_t pwX, pwY, pwZ, pmX, pmY, pmZ;
+    double nx1, nx2;                  // uniforms of the event after the next one
 };
 
 struct Dyn {
@@ -98,26 +106,32 @@ struct Dyn {
     int32_t* disp;
     int32_t* aff;
     uint8_t* hop_sp;
+    uint8_t* wsp;     // window species [2 W^3] (single-vacancy path)
+    int32_t* wrho;    // window densities [2 W^3]
+    int32_t* dprev;   // window path: density change of the last hop, [8 dirs][4 atoms][145 read-set sites]
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Offsets of the dynamic shared-memory arrays (16-byte aligned).
 struct DynLayout {
-    size_t off[12];
+    size_t off[15];
     size_t total;
 };
 
-__host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P) {
-    const size_t sz[12] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
+__host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) {
+    const size_t nw = 2 * (size_t)win * win * win;
+    const size_t sz[15] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
                            sizeof(double) * 8 * max_nv, sizeof(double) * 8 * max_nv,
                            sizeof(double) * kEtab,      sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * 3 * max_nv,
-                           sizeof(int32_t) * max_nv,    (size_t)8 * max_nv};
+                           sizeof(int32_t) * max_nv,    (size_t)8 * max_nv,
+                           nw,                          sizeof(int32_t) * nw,
+                           win > 0 ? sizeof(int32_t) * kEamU * 32 : 0};
     DynLayout l;
     size_t o = 0;
-    for (int i = 0; i < 12; ++i) {
+    for (int i = 0; i < 15; ++i) {
         l.off[i] = o;
         o = align16(o + sz[i]);
     }
@@ -125,8 +139,8 @@ __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P) {
     return l;
 }
 
-__device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P) {
-    const DynLayout l = dyn_layout(max_nv, max_P);
+__device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P, int win) {
+    const DynLayout l = dyn_layout(max_nv, max_P, win);
     Dyn d;
     d.tree = (double*)(base + l.off[0]);
     d.rates = (double*)(base + l.off[1]);
@@ -140,10 +154,14 @@ __device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P)
     d.disp = (int32_t*)(base + l.off[9]);
     d.aff = (int32_t*)(base + l.off[10]);
     d.hop_sp = (uint8_t*)(base + l.off[11]);
+    d.wsp = win > 0 ? (uint8_t*)(base + l.off[12]) : nullptr;
+    d.wrho = win > 0 ? (int32_t*)(base + l.off[13]) : nullptr;
+    d.dprev = win > 0 ? (int32_t*)(base + l.off[14]) : nullptr;
     return d;
 }
 
-size_t step_dyn_smem(int max_nv, int max_P) { return dyn_layout(max_nv, max_P).total; }
+size_t step_dyn_smem(int max_nv, int max_P, int win) { return dyn_layout(max_nv, max_P, win).total; }
+
 
 // Order of non-negative doubles equals the order of their bit patterns.
 __device__ __forceinline__ bool lt_nonneg(double a, double b) {
@@ -227,7 +245,7 @@ __device__ __forceinline__ long long embed_q(const StepShared& S, int a, int r, 
     const float t = (float)(r - (k << S.shift)) * S.inv_knot_f;
     const float4 c = __ldg(&S.Ff[a * last + k]);
     const float p = t * (c.x + t * (c.y + t * c.z));
-    return __ldg(&S.Fq[a * S.n_rho + k]) + ((long long)__float2int_rn(p * 4294967296.0f) << 8);
+    return __ldg(&S.Fq[a * S.n_rho + k]) + (long long)__float2int_rn(p * 4294967296.0f) * 256;
 }
 
 __device__ __forceinline__ double embed_fp64(const StepShared& S, int a, int r, int& bad) {
@@ -793,11 +811,426 @@ __device__ void run_events(StepShared& S, const Dyn& D, uint64_t target) {
     flush_clock<NW>(S);
 }
 
+// ---- single-vacancy path: lattice window in shared memory -------------------
+// A voxel with one vacancy keeps a window of W^3 cells (W = min(L, 16); species
+// and, for EAM, densities) around the vacancy in shared memory, so no read of
+// an event touches global memory.  Every change is written through to the
+// lattice in global memory as well (species stores, density atomics), and the
+// window is reloaded, centred on the vacancy, when the vacancy comes within 2
+// cells of its edge (all stencils of the vacancy and of its 8 targets reach at
+// most 4 half units).  An event takes two phases:
+//  A  warp 0: the 8 rates from the hop sums (a4), their subtree sums (a5) and
+//     the selection (a6) in lanes 0..7, then the swap (a7); the vacancy's
+//     coordinates live in registers and the 8 candidate moves are prepared
+//     lane-parallel while the float64 chain runs (on GB300 every float64 warp
+//     instruction holds the SM sub-partition's FP64 pipe for ~64 cycles, so
+//     the chain is kept to the operations the rate arithmetic needs);
+//     meanwhile the other warps add the previous hop's density change (a7) to
+//     the window and to memory and draw the uniforms of the next event;
+//  B  every warp: the energy changes of the 8 hops of the moved vacancy (a2,
+//     a3), reading the window (which lags by the hop just made) and adding
+//     that hop's density change from a table; one warp (two for 16 warps) per
+//     hop, exact integer sums reduced with warp reductions.
+// The arithmetic of every rate, sum and comparison is the one of the general
+// path, so the two give identical trajectories.
+
+__device__ __forceinline__ int widx(int X, int Y, int Z, int W) {
+    return ((((Z >> 1) * W + (Y >> 1)) * W + (X >> 1)) << 1) | (X & 1);
+}
+
+// Window-index difference of the site at packed offset o from a site of parity b.
+__device__ __forceinline__ int wdelta(int b, int32_t o, int W) {
+    const int B = 4 + b;
+    return widx(B + off_dx(o), B + off_dy(o), B + off_dz(o), W) - widx(B, B, B, W);
+}
+
+// Thread 0: centre the window on the vacancy at global half-unit (X, Y, Z).
+__device__ __forceinline__ void window_center(StepShared& S, int X, int Y, int Z) {
+    const int W = S.W, L = S.v.L;
+    auto org = [&](int G) { const int o = (G >> 1) - W / 2; return o < 0 ? o + L : o; };
+    auto loc = [&](int G, int o) { const int l = G - 2 * o; return l < 0 ? l + 2 * L : l; };
+    S.ox = org(X);
+    S.oy = org(Y);
+    S.oz = org(Z);
+    S.lX = loc(X, S.ox);
+    S.lY = loc(Y, S.oy);
+    S.lZ = loc(Z, S.oz);
+    S.wb = widx(S.lX, S.lY, S.lZ, W);
+}
+
+// All threads: load the window at the current origin (L2 loads that bypass L1,
+// so the density atomics of this CTA are seen).
+template <int NW, int MODE>
+__device__ void window_load(StepShared& S, const Dyn& D) {
+    constexpr int NT = NW * 32;
+    const int W = S.W, L = S.v.L, ox = S.ox, oy = S.oy, oz = S.oz;
+    const int n = 2 * W * W * W;
+    const uint8_t* sp = S.v.species;
+    const int32_t* rho = S.v.rho;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n; j += NT) {
+        const int c = j >> 1;
+        const int lx = c % W, r = c / W, ly = r % W, lz = r / W;
+        int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+        gx -= gx >= L ? L : 0;
+        gy -= gy >= L ? L : 0;
+        gz -= gz >= L ? L : 0;
+        const size_t g = ((((size_t)gz * L + gy) * L + gx) << 1) | (size_t)(j & 1);
+        D.wsp[j] = __ldcg(sp + g);
+        if (MODE != 0) D.wrho[j] = __ldcg(rho + g);
+    }
+}
+
+// Embedding (split precision) with the table constants in registers; same
+// arithmetic as embed_q.
+struct EmbedC {
+    const float4* Ff;
+    const long long* Fq;
+    int last, shift;
+    float inv_knot;
+};
+
+__device__ __forceinline__ long long embed_c(const EmbedC& E, int a, int r, int& bad) {
+    int k = r >> E.shift;
+    if (r < 0 || k > E.last || (k == E.last && (r & ((1 << E.shift) - 1)))) bad = 1;
+    k = min(max(k, 0), E.last - 1);
+    const float t = (float)(r - (k << E.shift)) * E.inv_knot;
+    const float4 c = __ldg(&E.Ff[a * E.last + k]);
+    const float p = t * (c.x + t * (c.y + t * c.z));
+    return __ldg(&E.Fq[a * (E.last + 1) + k]) + (long long)__float2int_rn(p * 4294967296.0f) * 256;
+}
+
+// Exact sum over the warp of integers below 2^48 in magnitude (two 32-bit
+// warp reductions: of the low 24 bits and of the rest).
+__device__ __forceinline__ long long warp_sum_exact(long long v) {
+    const unsigned lo = (unsigned)(v & 0xFFFFFF);
+    const int hi = (int)(v >> 24);
+    const unsigned slo = __reduce_add_sync(0xffffffffu, lo);
+    const int shi = __reduce_add_sync(0xffffffffu, hi);
+    return (long long)shi * 16777216LL + (long long)slo;
+}
+
+// The float64 value q * 2^-24 of an integer q, built from its bits (exact).
+__device__ __forceinline__ double q24_to_double(int q) {
+    if (q == 0) return 0.0;
+    const unsigned long long m = q < 0 ? (unsigned long long)(-(long long)q) : (unsigned long long)q;
+    const int e = 63 - __clzll((long long)m);                 // top bit, < 32
+    const unsigned long long mant = (m << (52 - e)) & 0xFFFFFFFFFFFFFull;
+    const unsigned long long bits = ((unsigned long long)(e - 24 + 1023) << 52) | mant |
+                                    (q < 0 ? 0x8000000000000000ull : 0ull);
+    return __longlong_as_double((long long)bits);
+}
+
+template <int NW, int MODE>
+__device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) {
+    static_assert(NW == 8 || NW == 16, "window path: 8 or 16 warps");
+    static_assert(MODE == 0 || MODE == 1, "window path: pair model or split-precision EAM");
+    constexpr int NT = NW * 32;
+    constexpr int WPH = NW / 8;                                     // warps per hop
+    constexpr int NE = MODE == 0 ? kPairE : kEamE;                  // entries per hop
+    constexpr int EJ = (NE + 32 * WPH - 1) / (32 * WPH);            // entries per lane
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = S.v.L, M2 = 2 * L;
+    if (tid == 0) {
+        S.W = L < kWinMax ? L : kWinMax;
+        window_center(S, D.X[0], D.Y[0], D.Z[0]);
+    }
+    // density change of a hop in direction d of atom A at read-set site u:
+    // dprev[(d * 4 + A) * kEamU + u] = f_A(r_uw) - f_A(r_um) (u fastest, so the
+    // lanes of a warp, which read different sites, hit different banks)
+    if (MODE != 0)
+        for (int i = tid; i < kEamU * 32; i += NT) {
+            const int u = i % kEamU, da = i / kEamU, d = da >> 2, A = da & 3;
+            const int ds = S.dsh[u][d];
+            D.dprev[i] = S.fq[A][ds >> 3] - S.fq[A][ds & 7];
+        }
+    __syncthreads();
+    const int W = S.W;
+    window_load<NW, MODE>(S, D);
+    // per-lane constants of phase B: entries of hop k = warp % 8 and their
+    // window offsets for both parities of the vacancy site
+    const int k = warp & 7, half = warp >> 3;
+    uint32_t en[EJ];
+    int dl0[EJ], dl1[EJ];
+#pragma unroll
+    for (int j = 0; j < EJ; ++j) {
+        const int e = half * 32 + lane + 32 * WPH * j;
+        en[j] = e < NE ? S.ent[k][e] : 0xFFFFFFFFu;
+        const bool site = e < NE && (MODE == 0 || !(en[j] >> 14));
+        const int32_t o = site ? S.off[en[j] & 0xff] : off_pack(0, 0, 0, 0);
+        dl0[j] = wdelta(0, o, W);
+        dl1[j] = wdelta(1, o, W);
+    }
+    const int32_t omk = S.off[S.mk[k]];
+    const int dm0 = wdelta(0, omk, W), dm1 = wdelta(1, omk, W);
+    const int mkk = S.mk[k];
+    EmbedC E;
+    E.Ff = S.Ff;
+    E.Fq = S.Fq;
+    E.last = S.n_rho - 1;
+    E.shift = S.shift;
+    E.inv_knot = S.inv_knot_f;
+    // per-thread constants of the density update (threads 32 .. 32+115)
+    const int ut = tid - 32;
+    const bool upd = MODE != 0 && ut >= 0 && ut < 2 * kSph;
+    const int uside = upd && ut >= kSph;
+    const int32_t uo = upd ? S.sph[uside ? ut - kSph : ut] : off_pack(0, 0, 0, 0);
+    const int ud0 = wdelta(0, uo, W), ud1 = wdelta(1, uo, W), ush = off_extra(uo);
+    // warp 0: the vacancy in registers; lane k's candidate move d = k
+    const int cdx = (lane & 1) ? -1 : 1, cdy = (lane & 2) ? -1 : 1, cdz = (lane & 4) ? -1 : 1;
+    int gX = D.X[0], gY = D.Y[0], gZ = D.Z[0], lX = S.lX, lY = S.lY, lZ = S.lZ, wb = S.wb, pos = D.pos[0];
+    int disp0 = D.disp[0], disp1 = D.disp[1], disp2 = D.disp[2];
+    uint64_t n_ev = S.n;
+    const int log_cap = S.v.log_cap;
+    int32_t* const log = S.v.log;
+    uint8_t* const species = S.v.species;
+    const int hi_edge = 2 * W - 5;
+    __syncthreads();
+
+    int ccount = S.ccount;
+    uint64_t n_next = S.n + 1;       // event index whose uniforms the next phase A draws
+    bool first = true;
+    for (uint64_t done = 0;; ++done) {
+        const bool finish = done >= target;
+        // ---------------- phase A
+        if (warp == 0) {
+            if (lane < 8) {
+                // candidate move of this lane (integer work beside the float64 chain)
+                const int mX = wrap_coord(gX + cdx, M2), mY = wrap_coord(gY + cdy, M2), mZ = wrap_coord(gZ + cdz, M2);
+                const int mpos = site_index(mX, mY, mZ, L);
+                const int mlX = lX + cdx, mlY = lY + cdy, mlZ = lZ + cdz;
+                const int mwb = widx(mlX, mlY, mlZ, W);
+                const bool out = mlX < 4 || mlX > hi_edge || mlY < 4 || mlY > hi_edge || mlZ < 4 || mlZ > hi_edge;
+                const double u1 = S.nu1, u2 = S.nu2;
+                int A, dq = 0, bad;
+                double g;
+                if (first) {
+                    A = D.hop_sp[lane];
+                    g = D.rates[lane];
+                    bad = !finite_bits(g);
+                } else {
+                    A = S.hsp[lane];
+                    dq = MODE == 0 ? S.acc32[lane] : (int)((S.acc64[0][lane] + S.acc64[1][lane] + (1LL << 15)) >> 16);
+                    g = hop_rate_grid(S, D, A, dq);
+                    bad = S.hbad[0][lane] | S.hbad[1][lane] | !finite_bits(g);
+                }
+                const double s1 = g + __shfl_xor_sync(0xffu, g, 1);
+                const double s2 = s1 + __shfl_xor_sync(0xffu, s1, 2);
+                const double s3 = s2 + __shfl_xor_sync(0xffu, s2, 4);
+                bad = __any_sync(0xffu, bad);
+                // (a6) descent over the 3 levels of the vacancy's hop tree, the
+                // compares and subtractions of the general path, in every lane
+                const double R = s3;
+                double t = u1 * R;
+                const double h2 = __shfl_sync(0xffu, s2, 0), h3 = __shfl_sync(0xffu, s2, 4);
+                const double h4 = __shfl_sync(0xffu, s1, 0), h5 = __shfl_sync(0xffu, s1, 2);
+                const double h6 = __shfl_sync(0xffu, s1, 4), h7 = __shfl_sync(0xffu, s1, 6);
+                const double g0 = __shfl_sync(0xffu, g, 0), g1 = __shfl_sync(0xffu, g, 1);
+                const double g2 = __shfl_sync(0xffu, g, 2), g3 = __shfl_sync(0xffu, g, 3);
+                const double g4 = __shfl_sync(0xffu, g, 4), g5 = __shfl_sync(0xffu, g, 5);
+                const double g6 = __shfl_sync(0xffu, g, 6), g7 = __shfl_sync(0xffu, g, 7);
+                int d = 0;
+                if (!(lt_nonneg(t, h2) || is_zero(h3))) { t -= h2; d = 4; }
+                const double l2 = d ? h6 : h4, r2 = d ? h7 : h5;
+                if (!(lt_nonneg(t, l2) || is_zero(r2))) { t -= l2; d += 2; }
+                const double l3 = d == 0 ? g0 : d == 2 ? g2 : d == 4 ? g4 : g6;
+                const double r3 = d == 0 ? g1 : d == 2 ? g3 : d == 4 ? g5 : g7;
+                if (!(lt_nonneg(t, l3) || is_zero(r3))) d += 1;
+                // stored state of this event's rates (off the chain)
+                D.rates[lane] = g;
+                D.dE[lane] = (A == kVac || first) ? (first ? D.dE[lane] : 0.0) : q24_to_double(dq);
+                D.hop_sp[lane] = (uint8_t)A;
+                const bool trapped = !(__double_as_longlong(R) > 0);
+                const bool go = !finish && !bad && !S.numeric && !trapped;
+                if (go) {
+                    // (a7) the move of lane d: vacancy w -> m, atom Ad m -> w
+                    const int Ad = __shfl_sync(0xffu, A, d);
+                    const int nX = __shfl_sync(0xffu, mX, d), nY = __shfl_sync(0xffu, mY, d);
+                    const int nZ = __shfl_sync(0xffu, mZ, d), npos = __shfl_sync(0xffu, mpos, d);
+                    const int nlX = __shfl_sync(0xffu, mlX, d), nlY = __shfl_sync(0xffu, mlY, d);
+                    const int nlZ = __shfl_sync(0xffu, mlZ, d), nwb = __shfl_sync(0xffu, mwb, d);
+                    const bool nout = __shfl_sync(0xffu, out, d);
+                    if (lane == 0) {
+                        D.wsp[wb] = (uint8_t)Ad;
+                        D.wsp[nwb] = (uint8_t)kVac;
+                        species[pos] = (uint8_t)Ad;
+                        species[npos] = (uint8_t)kVac;
+                        S.dir = d;
+                        S.A = Ad;
+                        S.wX = gX; S.wY = gY; S.wZ = gZ;
+                        S.mX = nX; S.mY = nY; S.mZ = nZ;
+                        S.lX = nlX; S.lY = nlY; S.lZ = nlZ;
+                        S.wb = nwb;
+                        S.recenter = nout;
+                        const int c = ccount;
+                        S.cu2[c] = u2;
+                        S.cR[c] = R;
+                        if (log_cap > 0) log[n_ev % (uint64_t)log_cap] = d;
+                    }
+                    disp0 += (d & 1) ? -1 : 1;
+                    disp1 += (d & 2) ? -1 : 1;
+                    disp2 += (d & 4) ? -1 : 1;
+                    gX = nX; gY = nY; gZ = nZ;
+                    lX = nlX; lY = nlY; lZ = nlZ;
+                    wb = nwb;
+                    pos = npos;
+                    n_ev += 1;
+                }
+                if (lane == 0) {
+                    D.tree[1] = R;
+                    if (bad) S.numeric = 1;
+                    if (!finish && !go) {
+                        S.v.status = (bad || S.numeric) ? kENUMERIC : kETRAPPED;
+                        S.stop = 1;
+                    }
+                    if (finish || !go) {
+                        S.recenter = 0;
+                        S.n = n_ev;
+                        S.ccount = ccount;
+                        D.pos[0] = pos;
+                        D.X[0] = gX;
+                        D.Y[0] = gY;
+                        D.Z[0] = gZ;
+                        D.disp[0] = disp0;
+                        D.disp[1] = disp1;
+                        D.disp[2] = disp2;
+                    }
+                }
+            }
+        } else {
+            if (upd && !first) {
+                // (a7) density change of the pending hop w -> m (atom pA now at w):
+                // rho_i += f_A(r_iw) over S(w), -= f_A(r_im) over S(m)
+                const int c = uside ? S.pm : S.pw, cb = uside ? S.pmb : S.pwb;
+                const int f = S.fq[S.pA][ush];
+                atomicAdd(&D.wrho[c + (cb ? ud1 : ud0)], uside ? -f : f);
+                const int cX = uside ? S.pmX : S.pwX, cY = uside ? S.pmY : S.pwY, cZ = uside ? S.pmZ : S.pwZ;
+                const int s = site_index(wrap_coord(cX + off_dx(uo), M2), wrap_coord(cY + off_dy(uo), M2),
+                                         wrap_coord(cZ + off_dz(uo), M2), L);
+                atomicAdd(&S.v.rho[s], uside ? -f : f);
+            }
+            if (tid == NT - 1 && !finish) {
+                // uniforms of the event after the one selected in this phase
+                const uint64_t uid = S.v.uid, seed = S.v.seed;
+                uint32_t c0 = (uint32_t)n_next, c1 = (uint32_t)(n_next >> 32), c2 = (uint32_t)uid,
+                         c3 = (uint32_t)(uid >> 32) & 0x7fffffffu;
+                philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+                S.nx1 = u53_to_double(((uint64_t)c0 << 21) | (c1 >> 11));
+                S.nx2 = u53_to_double((((uint64_t)c2 << 21) | (c3 >> 11)) + 1);
+            }
+        }
+        __syncthreads();
+        if (finish || S.stop) break;
+        first = false;
+        ++ccount;
+        ++n_next;
+        if (S.recenter) {
+            if (tid == 0) window_center(S, S.mX, S.mY, S.mZ);
+            __syncthreads();
+            window_load<NW, MODE>(S, D);
+            if (warp == 0) {
+                lX = S.lX;
+                lY = S.lY;
+                lZ = S.lZ;
+                wb = S.wb;
+            }
+            __syncthreads();
+        }
+        // ---------------- phase B
+        const int b = S.lX & 1, base = S.wb;
+        const int Ap = S.A, dp = S.dir;
+        const int A = D.wsp[base + (b ? dm1 : dm0)];
+        if (MODE == 0) {
+            int v = 0;
+            if (A != kVac) {
+#pragma unroll
+                for (int j = 0; j < EJ; ++j) {
+                    const uint32_t e = en[j];
+                    if (e == 0xFFFFFFFFu) continue;
+                    const int x = D.wsp[base + (b ? dl1[j] : dl0[j])], sh = (e >> 8) & 1;
+                    const int t = S.eps_q[sh][A * 5 + x] - S.eps_q[sh][kVac * 5 + x];
+                    v += (e >> 9) & 1 ? -t : t;
+                }
+            }
+            v = __reduce_add_sync(0xffffffffu, v);
+            if (lane == 0 && half == 0) {
+                S.acc32[k] = v;
+                S.hsp[k] = A;
+                S.hbad[0][k] = S.hbad[1][k] = 0;
+            }
+        } else {
+            long long v = 0;
+            int bad = 0;
+            if (A != kVac) {
+                const int* dpv = D.dprev + (dp * 4 + Ap) * kEamU;
+                const int32_t* fqA = S.fq[A];
+#pragma unroll
+                for (int j = 0; j < EJ; ++j) {
+                    const uint32_t e = en[j];
+                    if (e == 0xFFFFFFFFu) continue;
+                    if (e >> 14) {
+                        // the moving atom's own embedding: F_A(rho_w - f_A(1nn)) - F_A(rho_m)
+                        const int rp = D.wrho[base] + dpv[0];
+                        const int rm = D.wrho[base + (b ? dm1 : dm0)] + dpv[mkk];
+                        v += embed_c(E, A, rp - S.fq[A][1], bad) - embed_c(E, A, rm, bad);
+                    } else {
+                        const int idx = e & 0xff, sip = (e >> 8) & 7, sim = (e >> 11) & 7;
+                        const int wi = base + (b ? dl1[j] : dl0[j]);
+                        const int a = D.wsp[wi];
+                        const int r = D.wrho[wi] + dpv[idx];
+                        const int dka = fqA[sip] - fqA[sim];
+                        if (a == kVac) continue;
+                        const int pi = pair_index(A, a);
+                        v += embed_c(E, a, r + dka, bad) - embed_c(E, a, r, bad) +
+                             (S.phi_q[pi][sip] - S.phi_q[pi][sim]);
+                    }
+                }
+            }
+            v = warp_sum_exact(v);
+            bad = __any_sync(0xffffffffu, bad);
+            if (lane == 0) {
+                S.acc64[half][k] = v;
+                S.hbad[half][k] = bad;
+                if (WPH == 1) {
+                    S.acc64[1][k] = 0;
+                    S.hbad[1][k] = 0;
+                }
+                if (half == 0) S.hsp[k] = A;
+            }
+        }
+        if (tid == NT - 1) {
+            S.nu1 = S.nx1;
+            S.nu2 = S.nx2;
+            // the hop just made becomes the pending density change (window sites
+            // taken in the window as it is now, after any re-centring)
+            const int d = S.dir;
+            const int dx = (d & 1) ? -1 : 1, dy = (d & 2) ? -1 : 1, dz = (d & 4) ? -1 : 1;
+            S.pA = S.A;
+            S.pm = S.wb;
+            S.pmb = S.lX & 1;
+            S.pw = widx(S.lX - dx, S.lY - dy, S.lZ - dz, W);
+            S.pwb = S.pmb ^ 1;
+            S.pwX = S.wX; S.pwY = S.wY; S.pwZ = S.wZ;
+            S.pmX = S.mX; S.pmY = S.mY; S.pmZ = S.mZ;
+        }
+        __syncthreads();
+        if (ccount == kClockBatch) {
+            if (tid == 0) S.ccount = ccount;
+            __syncthreads();
+            flush_clock<NW>(S);
+            ccount = 0;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && S.numeric && S.v.status == kOK) S.v.status = kENUMERIC;
+    flush_clock<NW>(S);
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) step_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     __shared__ StepShared S;
-    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P);
+    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, a.win);
     load_model<NW>(S, a.model);
     __syncthreads();
     for (;;) {
@@ -817,12 +1250,24 @@ __global__ void __launch_bounds__(NW * 32) step_kernel(BatchArgs a) {
             load_voxel_state<NW>(S, D);
             __syncthreads();
             const int mode = S.v.model == 0 ? 0 : (S.v.precision == 1 ? 1 : 2);
-            if (mode == 0)
-                run_events<NW, 0>(S, D, S.target);
-            else if (mode == 1)
-                run_events<NW, 1>(S, D, S.target);
-            else
-                run_events<NW, 2>(S, D, S.target);
+            bool done = false;
+            if constexpr (NW >= 8) {
+                if (a.win > 0 && window_edge(S.v.L, S.v.nv, S.v.model, S.v.precision) > 0) {
+                    if (mode == 0)
+                        run_events_window<NW, 0>(S, D, S.target);
+                    else
+                        run_events_window<NW, 1>(S, D, S.target);
+                    done = true;
+                }
+            }
+            if (!done) {
+                if (mode == 0)
+                    run_events<NW, 0>(S, D, S.target);
+                else if (mode == 1)
+                    run_events<NW, 1>(S, D, S.target);
+                else
+                    run_events<NW, 2>(S, D, S.target);
+            }
             store_voxel_state<NW>(S, D, &a.vox[vid]);
         }
         __syncthreads();
@@ -836,7 +1281,7 @@ template <int NW>
 __global__ void __launch_bounds__(NW * 32) rebuild_kernel(BatchArgs a, const int32_t* list) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     __shared__ StepShared S;
-    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P);
+    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
     const int vid = list ? list[blockIdx.x] : (int)blockIdx.x;
     load_model<NW>(S, a.model);
     if (threadIdx.x == 0) S.v = a.vox[vid];
@@ -897,7 +1342,7 @@ cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, cons
 // by step_occupancy() for this batch shape (no runtime call other than the
 // launch happens here, so the launch can be captured in a CUDA graph).
 cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st) {
-    size_t dyn = step_dyn_smem(a.max_nv, a.max_P);
+    size_t dyn = step_dyn_smem(a.max_nv, a.max_P, a.win);
     switch (warps) {
 #define AKMC_CASE(W)                                                              \
     case W:                                                                       \
@@ -913,7 +1358,7 @@ cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st
 cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, int n_list, cudaStream_t st) {
     const int grid = list ? n_list : a.n_vox;
     if (grid == 0) return cudaSuccess;
-    size_t dyn = step_dyn_smem(a.max_nv, a.max_P);
+    size_t dyn = step_dyn_smem(a.max_nv, a.max_P, 0);
     cudaError_t e = cudaSuccess;
     switch (warps) {
 #define AKMC_CASE(W)                                                              \
@@ -934,8 +1379,8 @@ cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, i
 static std::mutex g_attr_mu;
 static size_t g_attr_max[64][17];
 
-int step_occupancy(int warps, int max_nv, int max_P) {
-    const size_t dyn = step_dyn_smem(max_nv, max_P);
+int step_occupancy(int warps, int max_nv, int max_P, int win) {
+    const size_t dyn = step_dyn_smem(max_nv, max_P, win);
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || warps < 1 || warps > 16) return 0;

@@ -21,7 +21,7 @@ def workload_key(descs):
     return tuple(sorted(c.items()))
 
 
-def tune(descs, model, events=2000, candidates=((8, 0), (4, 0), (2, 0), (8, 1), (4, 2)), sample=1024):
+def tune(descs, model, events=2000, candidates=((8, 0), (16, 0), (4, 0), (2, 0), (8, 1), (4, 2)), sample=1024):
     """Return (warps, ctas_per_sm) with the highest events/s on a scratch copy
     of up to `sample` of the voxels."""
     import torch

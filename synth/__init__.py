@@ -298,3 +298,29 @@ def random_lattice(L: int, n_vac: int, fracs=(0.1, 0.1, 0.1), seed: int = 0):
         species[perm[k:k + c]] = s
         k += c
     return species, vac
+
+
+def precipitate_lattice(L: int, n_vac: int, cube: int = 4, fracs_ni_mn=(0.01, 0.01), seed: int = 0):
+    """A lattice holding one compact Cu precipitate: every site of the cube of
+    `cube`^3 cells at the origin is Cu (2*cube^3 sites); Ni, Mn and the
+    vacancies are scattered at random over the rest.  Used to start ensembles
+    far from equilibrium, so that the dynamics visibly moves the cluster
+    histogram.  Returns (species uint8[2L^3], vac_pos int32[n_vac])."""
+    n = 2 * L ** 3
+    species = np.zeros(n, dtype=np.uint8)
+    s = np.arange(n)
+    c = s >> 1
+    x, y, z = c % L, (c // L) % L, c // (L * L)
+    in_cube = (x < cube) & (y < cube) & (z < cube)
+    species[in_cube] = CU
+    rest = np.flatnonzero(~in_cube)
+    rng = np.random.default_rng([seed, L, n_vac, cube])
+    perm = rng.permutation(rest)
+    vac = perm[:n_vac].astype(np.int32)
+    species[vac] = VAC
+    k = n_vac
+    for sp, fr in zip((NI, MN), fracs_ni_mn):
+        cnt = int(math.floor(fr * n + 0.5))
+        species[perm[k:k + cnt]] = sp
+        k += cnt
+    return species, vac

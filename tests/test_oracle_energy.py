@@ -210,3 +210,29 @@ def test_detailed_balance(model, wild_model, mdl, L, wild):
                 assert g_f / g_r == pytest.approx(expect, rel=1e-12)
     if wild and mdl == 0:
         assert clamp_hits > 0   # the wild table exercises the clamped branches
+
+
+def test_density_brute_force(model):
+    """rho_i = sum over non-vacancy sites j within the cutoff of f_{s_j}(r_ij),
+    by minimal-image distances over all site pairs (no stencil tables)."""
+    L = 5
+    v = _voxel_from_lattice(model, L, 3, (0.1, 0.1, 0.1), 41, 1)
+    sp = v.state()["species"]
+    N = sp.size
+    s = np.arange(N)
+    c = s >> 1
+    b = s & 1
+    X = np.stack([2 * (c % L) + b, 2 * ((c // L) % L) + b, 2 * (c // (L * L)) + b], -1)
+    d = X[:, None, :] - X[None, :, :]
+    d = (d + L) % (2 * L) - L                       # minimal image in half units
+    r2 = (d ** 2).sum(-1)                           # (2 r / a)^2
+    shell_r2 = {3: 0, 4: 1, 8: 2, 11: 3, 12: 4}     # bcc shells 1-5 in half units
+    _, fq = oracle.shell_constants(model)
+    rho = np.zeros(N, np.int64)
+    for i in range(N):
+        for j in range(N):
+            k = shell_r2.get(int(r2[i, j]))
+            if k is not None and sp[j] != 4:
+                rho[i] += int(fq[sp[j]][k])
+    np.testing.assert_array_equal(v.rho_all(), rho)
+    assert all(v.rho_fixed(i) == rho[i] for i in range(0, N, 7))
