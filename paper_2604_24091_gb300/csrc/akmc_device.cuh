@@ -78,7 +78,7 @@ struct ModelDev {
     const double* f_tab;
     const double* F_tab;
     Cubic64* Fd;               // [4][n_rho-1]: F_k, c1, c2, c3 (FP64 Horner in t)
-    float4* Ff;                // [4][n_rho-1]: c1, c2, c3, 0 (FP32)
+    float4* Ff;                // [4][n_rho]: c1, c2, c3, 0 (FP32); the last knot of each species is all zero
     long long* Fq;             // [4][n_rho]: F_k in units of 2^-40 eV
 };
 

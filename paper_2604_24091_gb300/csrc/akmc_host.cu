@@ -243,7 +243,7 @@ akmc_status validate(const akmc_voxel_desc* descs, int32_t n, const akmc_model* 
         if (!(m->a > 0.0) || !(m->r_cut > m->a * std::sqrt(3.0)) || !(m->r_cut < 2.0 * m->a))
             return fail(AKMC_EINVAL, "r_cut must lie between the 5th and 6th bcc shells");
         int sh = rho_shift_of(m->rho_h);
-        if (sh < 0) return fail(AKMC_EINVAL, "rho_h must be a power of two in [2^-24, 1]");
+        if (sh < 0 || sh > 23) return fail(AKMC_EINVAL, "rho_h must be a power of two in [2^-24, 2^-1]");
         if ((double)(m->n_rho - 1) * std::ldexp(1.0, sh) >= 2147483648.0)
             return fail(AKMC_EINVAL, "embedding table too long for the fixed-point density");
         if (!all_finite(m->phi_tab, 20 * (size_t)m->n_r) || !all_finite(m->f_tab, 8 * (size_t)m->n_r) ||
@@ -294,7 +294,7 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         Lo.f_raw = take(sizeof(double) * 8 * m->n_r);
         Lo.F_raw = take(sizeof(double) * 8 * m->n_rho);
         Lo.Fd = take(sizeof(Cubic64) * 4 * (m->n_rho - 1));
-        Lo.Ff = take(sizeof(float4) * 4 * (m->n_rho - 1));
+        Lo.Ff = take(sizeof(float4) * 4 * m->n_rho);   // one zero pad per species at the last knot
         Lo.Fq = take(sizeof(long long) * 4 * m->n_rho);
         for (int32_t v = 0; v < n; ++v) {
             if (d[v].model != AKMC_EAM) continue;

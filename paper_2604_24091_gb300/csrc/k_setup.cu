@@ -93,7 +93,9 @@ __global__ void setup_model_kernel(ModelDev* M, int32_t* batch_status) {
                 double c2 = 3.0 * (F1 - F0) - (2.0 * d0 + d1);
                 double c3 = 2.0 * (F0 - F1) + (d0 + d1);
                 M->Fd[(size_t)a * nint + k] = Cubic64{F0, c1, c2, c3};
-                M->Ff[(size_t)a * nint + k] = make_float4((float)c1, (float)c2, (float)c3, 0.f);
+                M->Ff[i] = make_float4((float)c1, (float)c2, (float)c3, 0.f);
+            } else {
+                M->Ff[i] = make_float4(0.f, 0.f, 0.f, 0.f);   // the last knot itself: F = Fq exactly
             }
         }
     }

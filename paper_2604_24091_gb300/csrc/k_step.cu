@@ -232,20 +232,44 @@ __device__ void load_tables(StepShared& S, const Tables* T, int model, int small
     __syncthreads();
 }
 
-// Embedding function on the fixed-point density r: knot k = r >> shift,
-// t = (r - k*2^shift) 2^-shift (exact).  Outside the table: clamp, flag.
-// Split precision: the knot value is exact in 2^-40 eV; the Hermite part
-// t (c1 + t (c2 + t c3)) is evaluated in FP32 (|part| < 0.5 eV) and rounded
-// to 2^-32 eV; the result is one integer in units of 2^-40 eV.
-__device__ __forceinline__ long long embed_q(const StepShared& S, int a, int r, int& bad) {
-    const int last = S.n_rho - 1;
-    int k = r >> S.shift;
-    if (r < 0 || k > last || (k == last && (r & ((1 << S.shift) - 1)))) bad = 1;
-    k = min(max(k, 0), last - 1);
-    const float t = (float)(r - (k << S.shift)) * S.inv_knot_f;
-    const float4 c = __ldg(&S.Ff[a * last + k]);
+// Embedding function on the fixed-point density r (split precision): knot
+// k = r >> shift, t = (r - k 2^shift) 2^-shift, built exactly from the bits of
+// the remainder.  The knot value is exact in 2^-40 eV; the Hermite part
+// t (c1 + t (c2 + t c3)) is evaluated in FP32 (|part| < 0.5 eV) and rounded to
+// 2^-40 eV; the result is one integer in units of 2^-40 eV.  The coefficient
+// table has a zero entry at the last knot, so r = (n_rho - 1) 2^shift gives the
+// last knot value exactly; r outside [0, (n_rho - 1) 2^shift] is clamped to it
+// and flagged.
+struct EmbedC {
+    const float4* Ff;
+    const long long* Fq;
+    int n_rho, shift;
+    unsigned lim;      // (n_rho - 1) << shift
+};
+
+__device__ __forceinline__ long long embed_c(const EmbedC& E, int a, int r, int& bad) {
+    const unsigned ur = (unsigned)r;
+    bad |= ur > E.lim;
+    const unsigned k = min(ur >> E.shift, (unsigned)(E.n_rho - 1));
+    const float t = __int_as_float(0x3F800000 | ((ur & ((1u << E.shift) - 1u)) << (23 - E.shift))) - 1.0f;
+    const int i = a * E.n_rho + (int)k;
+    const float4 c = __ldg(&E.Ff[i]);
     const float p = t * (c.x + t * (c.y + t * c.z));
-    return __ldg(&S.Fq[a * S.n_rho + k]) + (long long)__float2int_rn(p * 4294967296.0f) * 256;
+    return __ldg(&E.Fq[i]) + __float2ll_rn(p * 1099511627776.0f);
+}
+
+__device__ __forceinline__ EmbedC embed_consts(const StepShared& S) {
+    EmbedC E;
+    E.Ff = S.Ff;
+    E.Fq = S.Fq;
+    E.n_rho = S.n_rho;
+    E.shift = S.shift;
+    E.lim = (unsigned)(S.n_rho - 1) << S.shift;
+    return E;
+}
+
+__device__ __forceinline__ long long embed_q(const StepShared& S, int a, int r, int& bad) {
+    return embed_c(embed_consts(S), a, r, bad);
 }
 
 __device__ __forceinline__ double embed_fp64(const StepShared& S, int a, int r, int& bad) {
@@ -881,25 +905,6 @@ __device__ void window_load(StepShared& S, const Dyn& D) {
     }
 }
 
-// Embedding (split precision) with the table constants in registers; same
-// arithmetic as embed_q.
-struct EmbedC {
-    const float4* Ff;
-    const long long* Fq;
-    int last, shift;
-    float inv_knot;
-};
-
-__device__ __forceinline__ long long embed_c(const EmbedC& E, int a, int r, int& bad) {
-    int k = r >> E.shift;
-    if (r < 0 || k > E.last || (k == E.last && (r & ((1 << E.shift) - 1)))) bad = 1;
-    k = min(max(k, 0), E.last - 1);
-    const float t = (float)(r - (k << E.shift)) * E.inv_knot;
-    const float4 c = __ldg(&E.Ff[a * E.last + k]);
-    const float p = t * (c.x + t * (c.y + t * c.z));
-    return __ldg(&E.Fq[a * (E.last + 1) + k]) + (long long)__float2int_rn(p * 4294967296.0f) * 256;
-}
-
 // Exact sum over the warp of integers below 2^48 in magnitude (two 32-bit
 // warp reductions: of the low 24 bits and of the rest).
 __device__ __forceinline__ long long warp_sum_exact(long long v) {
@@ -964,12 +969,7 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
     const int32_t omk = S.off[S.mk[k]];
     const int dm0 = wdelta(0, omk, W), dm1 = wdelta(1, omk, W);
     const int mkk = S.mk[k];
-    EmbedC E;
-    E.Ff = S.Ff;
-    E.Fq = S.Fq;
-    E.last = S.n_rho - 1;
-    E.shift = S.shift;
-    E.inv_knot = S.inv_knot_f;
+    const EmbedC E = embed_consts(S);
     // per-thread constants of the density update (threads 32 .. 32+115)
     const int ut = tid - 32;
     const bool upd = MODE != 0 && ut >= 0 && ut < 2 * kSph;
