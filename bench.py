@@ -52,10 +52,12 @@ EAM_BYTES_PER_EVENT = 145 * (1 + 4) + 2 + 78 * 4 * 2
 # Rate kernel (akmc_compute_rates) algorithmic bytes per site: read species
 # (1 B) and write the density (4 B).
 RATE_BYTES_PER_SITE = 5
-# DRAM bytes per step-kernel launch from the ncu capture summarised in
-# profiles/ (scaled to the full launch), valid only for the kernel source it
-# was taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": None, "bytes_per_event": None}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per event of one
+# full-size step-kernel launch, from one ncu capture of
+# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (545 MB read +
+# 5.38 GB written for 2.56e8 events); valid only for the kernel source it was
+# taken from.
+NCU_STEP_TRAFFIC = {"k_step_sha1": "733a5b1e84a42960c7c76b6f51af629dbd9f2f6c", "bytes_per_event": 23.15}
 
 
 def _step_src_sha1():
