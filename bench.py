@@ -359,6 +359,20 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
                     "persistent_one_voxel": n_pers / tp}
     p.close()
     out["rate_kernel_roofline"] = rate_kernel_leg(model, torch, peak, peak_kind, Batch)
+    # the uneven configuration (1000 voxels, L 16-64, 1-8 vacancies, pair/EAM)
+    # and the large one (128^3 cells, 64 vacancies): events/s of one persistent launch
+    for key, cfg, per_vac in (("uneven", synth.config_uneven(1000), 10000), ("large", synth.config_large(), 20000)):
+        ub = Batch(cfg, model)
+        tg = np.array([per_vac * d.n_vac for d in cfg], np.uint64) if key == "uneven" else \
+            np.full(len(cfg), per_vac, np.uint64)
+        ub.step(np.minimum(tg, 200).astype(np.uint64))
+        tu = _time_region(lambda: ub.step(tg), torch)
+        stu, _ = ub.sync_status()
+        out[key] = {"value": float(tg.sum()) / tu, "unit": UNIT, "status": stu,
+                    "config": ("1000 voxels, L in {16,24,32,48,64}, 1-8 vacancies, pair/EAM 50/50, "
+                               "1e4 events per vacancy" if key == "uneven" else
+                               "1 voxel of 128^3 cells, 64 vacancies, EAM split, 2e4 events")}
+        ub.close()
     # the oracle on the host cores, bounded sample of the same workload
     procs = os.cpu_count() or 1
     per = 3 * args.ref_events

@@ -296,3 +296,43 @@ def test_single_vacancy_fast_path_matches_oracle(model):
             o2 = oracle.Voxel(d, model)
             o2.load(g["species"], g["vac_pos"])
             assert np.abs(g["dE"] - o2.state()["dE"]).max() <= (1e-12 if d.precision == 0 else SPLIT_DE_TOL)
+
+
+def test_large_voxel_sampled(model):
+    # The large configuration (one voxel of 128^3 cells, 64 vacancies, EAM split):
+    # conservation, exact densities after the events, and every hop energy change of
+    # all 64 vacancies within the split tolerance on the GPU's final lattice.
+    d = synth.config_large()[0]
+    b = Batch([d], model)
+    b.step(3000)
+    st, per = b.sync_status()
+    assert st == 0
+    g = b.read_state(0)
+    assert g["n_events"] == 3000
+    o = oracle.Voxel(d, model)
+    assert np.array_equal(np.bincount(g["species"], minlength=5), np.bincount(o.state()["species"], minlength=5))
+    o.load(g["species"], g["vac_pos"])
+    np.testing.assert_array_equal(b.read_density(0).astype(np.int64), o.rho_all())
+    so = o.state()
+    assert np.abs(g["dE"] - so["dE"]).max() <= SPLIT_DE_TOL
+    _assert_rates(g["rates"], so["rates"], rtol=1e-3)
+    b.close()
+
+
+def test_large_voxel_fp64_trajectory(model):
+    # 128^3 cells with 64 vacancies in FP64: the event sequence of the general
+    # (multi-vacancy, incremental tree) path matches the oracle event by event.
+    d = synth.VoxelDesc(128, 64, (0.002, 0.007, 0.014), 563.0, synth.EAM_MODEL, synth.PREC_FP64,
+                        synth.splitmix64(synth.SEED_BASE + 4, 0), 0)
+    n = 400
+    b = Batch([d], model, event_log_capacity=n)
+    b.step(n)
+    g = b.read_state(0, log=True)
+    o = oracle.Voxel(d, model)
+    log_o = o.step(n, log=True)
+    assert np.array_equal(g["event_log"], log_o)
+    so = o.state()
+    assert np.array_equal(g["species"], so["species"])
+    _assert_rates(g["rates"], so["rates"])
+    assert abs(_time(g) - _time(so)) <= 1e-12 * _time(so)
+    b.close()
