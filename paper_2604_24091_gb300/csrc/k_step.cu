@@ -106,8 +106,8 @@ struct Dyn {
     int32_t* disp;
     int32_t* aff;
     uint8_t* hop_sp;
-    uint8_t* wsp;     // window species [2 W^3] (single-vacancy path)
-    int32_t* wrho;    // window densities [2 W^3]
+    uint8_t* wsp;     // window species (single-vacancy path; padded layout, see widx)
+    int32_t* wrho;    // window densities (same layout)
     int32_t* dprev;   // window path: density change of the last hop, [8 dirs][4 atoms][145 read-set sites]
 };
 
@@ -119,8 +119,10 @@ struct DynLayout {
     size_t total;
 };
 
+__host__ __device__ inline int win_sites(int W);
+
 __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) {
-    const size_t nw = 2 * (size_t)win * win * win;
+    const size_t nw = win > 0 ? (size_t)win_sites(win) : 0;
     const size_t sz[15] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
                            sizeof(double) * 8 * max_nv, sizeof(double) * 8 * max_nv,
                            sizeof(double) * kEtab,      sizeof(int32_t) * max_nv,
@@ -858,8 +860,14 @@ __device__ void run_events(StepShared& S, const Dyn& D, uint64_t target) {
 // The arithmetic of every rate, sum and comparison is the one of the general
 // path, so the two give identical trajectories.
 
+// Window layout: a row (fixed cell y, z) holds the 2W sites X = 2x + b in order;
+// rows are padded to 2W + 1 sites and planes to W (2W + 1) + 8, so that sites
+// in neighbouring rows and planes fall in different shared-memory banks.
+__host__ __device__ inline int win_sites(int W) { return W * (W * (2 * W + 1) + 8); }
+
 __device__ __forceinline__ int widx(int X, int Y, int Z, int W) {
-    return ((((Z >> 1) * W + (Y >> 1)) * W + (X >> 1)) << 1) | (X & 1);
+    const int RS = 2 * W + 1, PS = W * RS + 8;
+    return (Z >> 1) * PS + (Y >> 1) * RS + X;
 }
 
 // Window-index difference of the site at packed offset o from a site of parity b.
@@ -893,15 +901,16 @@ __device__ void window_load(StepShared& S, const Dyn& D) {
     const int32_t* rho = S.v.rho;
 #pragma unroll 4
     for (int j = threadIdx.x; j < n; j += NT) {
-        const int c = j >> 1;
+        const int c = j >> 1, bb = j & 1;
         const int lx = c % W, r = c / W, ly = r % W, lz = r / W;
         int gx = ox + lx, gy = oy + ly, gz = oz + lz;
         gx -= gx >= L ? L : 0;
         gy -= gy >= L ? L : 0;
         gz -= gz >= L ? L : 0;
-        const size_t g = ((((size_t)gz * L + gy) * L + gx) << 1) | (size_t)(j & 1);
-        D.wsp[j] = __ldcg(sp + g);
-        if (MODE != 0) D.wrho[j] = __ldcg(rho + g);
+        const size_t g = ((((size_t)gz * L + gy) * L + gx) << 1) | (size_t)bb;
+        const int w = widx(2 * lx + bb, 2 * ly + bb, 2 * lz + bb, W);
+        D.wsp[w] = __ldcg(sp + g);
+        if (MODE != 0) D.wrho[w] = __ldcg(rho + g);
     }
 }
 
