@@ -321,6 +321,26 @@ def rate_kernel_leg(model, torch, peak, peak_kind, Batch):
             "ms": 1e3 * min(ts)}
 
 
+def logit_select_leg(torch, dev, peak, peak_kind):
+    """Global masked softmax sampling (akmc_select_logits) over 256 systems of
+    65536 agents x 8 candidate transitions (134 M float32 logits + uint8 mask,
+    671 MB > L2); algorithmic bytes 5 per logit (each logit and mask byte read
+    once).  Best of 5 calls."""
+    from paper_2604_24091_gb300 import SelectPlan, select_logits
+    n_seg, per = 256, 65536 * 8
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_BASE + 6)
+    logits = torch.randn(n_seg * per, generator=g, device=dev, dtype=torch.float32) * 2.0
+    mask = (torch.rand(n_seg * per, generator=g, device=dev) < 0.02).to(torch.uint8)
+    plan = SelectPlan(np.arange(n_seg + 1, dtype=np.int64) * per)
+    select_logits(plan, logits, 1.0, 1, 0, mask)
+    ts = [_time_region(lambda c=c: select_logits(plan, logits, 1.0, 1, c + 1, mask), torch) for c in range(5)]
+    gbs = 5.0 * n_seg * per / min(ts) / 1e9
+    return {"bound": "hbm", "kernel": "akmc_select_logits (part max, part sums, search)", "achieved": gbs,
+            "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
+            "workload": "256 systems x 524288 logits (float32) + mask (uint8), 671 MB", "ms": 1e3 * min(ts)}
+
+
 def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
     out = {}
     # end to end through the public API with pinned host buffers: load the
@@ -359,6 +379,7 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
                     "persistent_one_voxel": n_pers / tp}
     p.close()
     out["rate_kernel_roofline"] = rate_kernel_leg(model, torch, peak, peak_kind, Batch)
+    out["logit_select_roofline"] = logit_select_leg(torch, dev, peak, peak_kind)
     # the uneven configuration (1000 voxels, L 16-64, 1-8 vacancies, pair/EAM)
     # and the large one (128^3 cells, 64 vacancies): events/s of one persistent launch
     for key, cfg, per_vac in (("uneven", synth.config_uneven(1000), 10000), ("large", synth.config_large(), 20000)):

@@ -244,6 +244,46 @@ int32_t akmc_n_voxels(const akmc_batch* batch);
 void akmc_destroy_batch(akmc_batch* batch);      /* never frees caller memory */
 const char* akmc_last_error(void);               /* thread-local, never NULL */
 
+/* ---- global masked softmax sampling (logit form of the event selection) ----
+ *
+ * The action distribution of Eq. (1)-(2): every agent i of a system proposes
+ * candidate transitions k with logits z_ik; admissible ones are scaled by 1/tau
+ * (tau > 0), inadmissible ones are -inf, and one softmax over the concatenated
+ * logits of all agents of the system selects one transition.  With
+ * z = ln(Gamma) and tau = 1 this is the rejection-free selection (probability
+ * Gamma / Gamma_tot).
+ *
+ * Input: one flat float32 device array of logits holding n_seg systems
+ * ("segments") back to back; segment s covers [offsets[s], offsets[s+1]).
+ * A logit is admissible iff mask[j] != 0 (mask: uint8 device array of the same
+ * length, or NULL) and it is finite.  Segments may be empty and up to 2^30 long.
+ *
+ * Method (exact and independent of the launch shape): M = max of z/tau over the
+ * admissible logits of the segment; weights q_j = round(exp(z_j/tau - M) 2^32)
+ * (FP32 exp), summed exactly in int64; u from Philox4x32-10 with key = seed and
+ * counter (counter_lo, counter_hi, s, 0x53454c45); t = floor(u W); the selected
+ * logit is the first whose running sum of q exceeds t.
+ *
+ * akmc_select_scratch_bytes: device scratch needed for these offsets (host
+ * array of n_seg+1 non-decreasing int64); 0 if the offsets are invalid.
+ * akmc_select_plan: validates the offsets and writes the work plan into the
+ * caller's scratch (256-byte aligned device memory, bytes >= the size above);
+ * returns the number of parts in *n_parts; synchronises the stream.  The plan
+ * stays valid for any number of akmc_select_logits calls with the same offsets.
+ * akmc_select_logits: stream-ordered (three kernels, no host synchronisation,
+ * capturable in a CUDA graph).  Outputs (device, n_seg entries): out_index[s] =
+ * offset of the selected logit within segment s, or -1 if the segment has no
+ * admissible logit; out_logp[s] = log of its probability (float32; NaN if none).
+ * Errors: AKMC_EINVAL for NULL pointers, tau <= 0 or not finite, or n_seg /
+ * n_parts that do not come from a plan; AKMC_ENOMEM if the scratch is too small.
+ */
+size_t akmc_select_scratch_bytes(const int64_t* host_offsets, int32_t n_seg);
+akmc_status akmc_select_plan(const int64_t* host_offsets, int32_t n_seg, void* scratch, size_t bytes,
+                             int32_t* n_parts, akmc_stream stream);
+akmc_status akmc_select_logits(const float* logits, const uint8_t* mask, int32_t n_seg, int32_t n_parts, float tau,
+                               uint64_t seed, uint64_t counter, const void* scratch, int64_t* out_index,
+                               float* out_logp, akmc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

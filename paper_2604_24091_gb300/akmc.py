@@ -77,6 +77,9 @@ def load_library():
             "akmc_batch_vacancies": (ctypes.c_int64, [P]),
             "akmc_cluster_hist": (I32, [P, I32, I32, P, P]),
             "akmc_read_density": (I32, [P, I32, P, P]),
+            "akmc_select_scratch_bytes": (SZ, [P, I32]),
+            "akmc_select_plan": (I32, [P, I32, P, SZ, P, P]),
+            "akmc_select_logits": (I32, [P, P, I32, I32, ctypes.c_float, U64, U64, P, P, P, P]),
             "akmc_cluster_hist_noalloc": (I32, [P, I32, I32, P, P]),
             "akmc_set_launch": (I32, [P, I32, I32]),
             "akmc_n_voxels": (I32, [P]),
@@ -336,3 +339,53 @@ class Batch:
         h = np.zeros(8, np.int64)
         _check(self._lib.akmc_cluster_hist(self._h, int(voxel), int(mode), _ptr(h), _stream_ptr(stream)))
         return h
+
+
+class SelectPlan:
+    """Work plan and device scratch of the global masked softmax sampler for
+    one segmentation (CSR offsets of the systems' concatenated logits)."""
+
+    def __init__(self, offsets, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("akmc needs a CUDA device; there is no CPU fallback")
+        lib = load_library()
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n_seg = int(self.offsets.size - 1)
+        nbytes = lib.akmc_select_scratch_bytes(_ptr(self.offsets), self.n_seg)
+        if nbytes == 0:
+            raise AkmcError(EINVAL, "invalid segment offsets")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.scratch = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+        n_parts = ctypes.c_int32()
+        _check(lib.akmc_select_plan(_ptr(self.offsets), self.n_seg, ctypes.c_void_p(self.scratch.data_ptr()),
+                                    int(nbytes), ctypes.byref(n_parts), _stream_ptr(stream)))
+        self.n_parts = int(n_parts.value)
+        self.device = dev
+
+
+def select_logits(plan, logits, tau=1.0, seed=0, counter=0, mask=None, out_index=None, out_logp=None,
+                  stream=None):
+    """Draw one logit per segment from softmax(z/tau) over the admissible logits
+    (Eq. 1-2).  logits: float32 CUDA tensor covering the plan's offsets; mask:
+    optional uint8 CUDA tensor of the same length.  Returns (index, logp) CUDA
+    tensors (int64 offset within the segment or -1; float32 log-probability)."""
+    import torch
+    lib = load_library()
+    if logits.dtype != torch.float32 or not logits.is_cuda or not logits.is_contiguous():
+        raise AkmcError(EINVAL, "logits must be a contiguous float32 CUDA tensor")
+    if logits.numel() < int(plan.offsets[-1]):
+        raise AkmcError(EINVAL, "logits shorter than the plan's offsets")
+    if mask is not None and (mask.dtype != torch.uint8 or not mask.is_cuda or mask.numel() < logits.numel()):
+        raise AkmcError(EINVAL, "mask must be a uint8 CUDA tensor as long as the logits")
+    if out_index is None:
+        out_index = torch.empty(plan.n_seg, dtype=torch.int64, device=logits.device)
+    if out_logp is None:
+        out_logp = torch.empty(plan.n_seg, dtype=torch.float32, device=logits.device)
+    _check(lib.akmc_select_logits(ctypes.c_void_p(logits.data_ptr()),
+                                  ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
+                                  plan.n_seg, plan.n_parts, float(tau), int(seed) & (2 ** 64 - 1),
+                                  int(counter) & (2 ** 64 - 1), ctypes.c_void_p(plan.scratch.data_ptr()),
+                                  ctypes.c_void_p(out_index.data_ptr()), ctypes.c_void_p(out_logp.data_ptr()),
+                                  _stream_ptr(stream)))
+    return out_index, out_logp

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libakmc.so")
-SOURCES = ["akmc_host.cu", "k_setup.cu", "k_density.cu", "k_step.cu", "k_cluster.cu"]
+SOURCES = ["akmc_host.cu", "k_setup.cu", "k_density.cu", "k_step.cu", "k_cluster.cu", "k_select.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
