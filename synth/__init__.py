@@ -324,3 +324,22 @@ def precipitate_lattice(L: int, n_vac: int, cube: int = 4, fracs_ni_mn=(0.01, 0.
         species[perm[k:k + cnt]] = sp
         k += cnt
     return species, vac
+
+
+def vacancy_solute_states(L: int, solute: int = CU):
+    """Every lattice of L^3 cells holding one vacancy and one solute atom in Fe:
+    returns (vac_sites int32[n], solute_sites int32[n], species uint8[n, 2L^3]),
+    n = N (N - 1) with N = 2L^3, ordered by (vacancy site, solute site)."""
+    N = 2 * L ** 3
+    vs, cs = [], []
+    for v in range(N):
+        for c in range(N):
+            if c != v:
+                vs.append(v)
+                cs.append(c)
+    vs = np.array(vs, np.int32)
+    cs = np.array(cs, np.int32)
+    sp = np.zeros((vs.size, N), np.uint8)
+    sp[np.arange(vs.size), vs] = VAC
+    sp[np.arange(vs.size), cs] = solute
+    return vs, cs, sp
