@@ -258,11 +258,16 @@ const char* akmc_last_error(void);               /* thread-local, never NULL */
  * A logit is admissible iff mask[j] != 0 (mask: uint8 device array of the same
  * length, or NULL) and it is finite.  Segments may be empty and up to 2^30 long.
  *
- * Method (exact and independent of the launch shape): M = max of z/tau over the
- * admissible logits of the segment; weights q_j = round(exp(z_j/tau - M) 2^32)
- * (FP32 exp), summed exactly in int64; u from Philox4x32-10 with key = seed and
- * counter (counter_lo, counter_hi, s, 0x53454c45); t = floor(u W); the selected
- * logit is the first whose running sum of q exceeds t.
+ * Method (integer sums, so the draw does not depend on the launch shape): the
+ * scaled logit is z * (1/tau) in FP32.  A segment is cut into parts of up to
+ * 8192 logits; part p has maximum m_p and weights q_j = round(exp(z_j/tau -
+ * m_p) 2^32) (FP32 exp) with exact int64 sum S_p.  With M = max m_p, the part
+ * weights w_p = round(S_p exp(m_p - M)) (exactly S_p for a one-part segment);
+ * u from Philox4x32-10 with key = seed and counter (counter_lo, counter_hi, s,
+ * 0x53454c45); t = floor(u W), W = sum w_p; the part whose running sum of w
+ * first exceeds t, then t - (the parts before) in the part's own units
+ * (times S_p / w_p, rounded down), then the logit whose running sum of q first
+ * exceeds that.
  *
  * akmc_select_scratch_bytes: device scratch needed for these offsets (host
  * array of n_seg+1 non-decreasing int64); 0 if the offsets are invalid.

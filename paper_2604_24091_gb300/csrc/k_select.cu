@@ -4,17 +4,18 @@
 // global softmax per segment, one transition drawn from it).
 //
 // A segment is one system (one voxel): the concatenated logits of all of its
-// agents.  Three stream-ordered launches, each spread over "parts" of at most
-// 65536 logits so that long and short segments balance across the SMs:
-//   1. part maxima of z/tau over admissible entries;
-//   2. with the segment maximum M, the weights w = exp(z/tau - M) (FP32 exp)
-//      in fixed point q = rn(w 2^32), summed exactly per 2048-logit tile and
-//      per part (int64; the sums do not depend on the summation order, so the
-//      draw does not depend on the launch shape);
-//   3. per segment: W = sum of q, t = floor(u W) for the segment's uniform u,
-//      then the part, the tile and the logit whose running sum first exceeds t
-//      (inverse-CDF search over the exact integer prefix sums).
-// Logits are read coalesced (one warp reads 32 consecutive logits per load).
+// agents.  It is cut into parts of at most 8192 logits (4 tiles of 2048).
+//   1. One CTA per part reads the part once (16-byte loads where aligned) into
+//      registers, takes its maximum m_p of z/tau (z * (1/tau), rounded once)
+//      and its weights q = rn(exp(z/tau - m_p) 2^32) (FP32 exp), summed exactly
+//      in int64 per tile and per part (S_p).
+//   2. One CTA per segment: M = max m_p; part weights w_p = rn(S_p exp(m_p - M))
+//      (integers); t = floor(u W) for W = sum w_p and the segment's uniform u;
+//      the part whose running sum of w first exceeds t; inside it t scaled to
+//      the part's own units, floor((t - before) S_p / w_p); then the tile and
+//      the logit whose running sum of q first exceeds that.  Every sum is an
+//      exact integer, so the draw does not depend on the launch shape, and a
+//      segment of one part is an exact inverse-CDF draw over its q.
 #include <akmc.h>
 
 #include <cmath>
@@ -31,8 +32,9 @@ namespace {
 constexpr int kSelThreads = 256;
 constexpr int kSelPerThread = 8;
 constexpr int kSelTile = kSelThreads * kSelPerThread;   // 2048 logits
-constexpr int kSelTilesPerPart = 32;
-constexpr int64_t kSelPart = (int64_t)kSelTile * kSelTilesPerPart;   // 65536 logits
+constexpr int kSelTilesPerPart = 4;
+constexpr int64_t kSelPart = (int64_t)kSelTile * kSelTilesPerPart;   // 8192 logits
+constexpr int kSelGroups = kSelPart / (4 * kSelThreads);              // float4 groups per thread (8)
 constexpr int64_t kSelMaxSegment = (int64_t)1 << 30;
 constexpr float kFix = 4294967296.0f;                   // weights in units of 2^-32
 constexpr uint32_t kSelStream = 0x53454c45u;            // Philox counter word 3 of the draws
@@ -70,13 +72,9 @@ SelLayout sel_layout(int n_seg, int n_parts) {
 }
 
 // Admissible iff the mask (when given) is nonzero and the logit is finite (a
-// logit of -inf is the masked value of Eq. 1).
-__device__ __forceinline__ bool sel_load(const float* z, const uint8_t* mask, int64_t j, float tau, float& zh) {
-    const float v = z[j];
-    const bool ok = (mask == nullptr || mask[j] != 0) && isfinite(v);
-    zh = __fdiv_rn(v, tau);
-    return ok;
-}
+// logit of -inf is the masked value of Eq. 1).  The scaled logit is z * (1/tau)
+// (rounded once; every pass uses the same expression).
+__device__ __forceinline__ bool sel_ok(float v, uint32_t mbyte) { return mbyte != 0 && isfinite(v); }
 
 __device__ __forceinline__ float block_max(float v, float* sm) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -110,139 +108,198 @@ __device__ __forceinline__ long long block_sum(long long v, long long* sm) {
     return v;
 }
 
-__device__ __forceinline__ long long sel_weight(float zh, bool ok, float M) {
-    return ok ? __float2ll_rn(expf(zh - M) * kFix) : 0;
+__device__ __forceinline__ long long sel_weight(float v, bool ok, float inv_tau, float M) {
+    return ok ? __float2ll_rn(expf(v * inv_tau - M) * kFix) : 0;
 }
 
-__global__ void __launch_bounds__(kSelThreads) sel_max_kernel(const float* z, const uint8_t* mask, float tau,
-                                                              const SelPart* parts, float* pmax) {
-    __shared__ float sm[32];
+// One CTA per part: the part's logits in registers (thread i holds the 4
+// consecutive logits at begin + 1024 g + 4 i of every group g), the part
+// maximum m_p of the scaled logits (the maximum of the raw admissible logits
+// times 1/tau: multiplication by a positive constant keeps the order), and the
+// exact tile and part sums of q = rn(exp(z/tau - m_p) 2^32).  Tile k holds
+// groups 2k and 2k + 1.
+__global__ void __launch_bounds__(kSelThreads) sel_part_kernel(const float* z, const uint8_t* mask, float inv_tau,
+                                                               const SelPart* parts, float* pmax, long long* psum,
+                                                               long long* tsum) {
+    __shared__ float smf[32];
+    __shared__ long long sml[32];
     const SelPart P = parts[blockIdx.x];
-    float m = -INFINITY;
-    for (int64_t j = P.begin + threadIdx.x; j < P.end; j += kSelThreads) {
-        float zh;
-        if (sel_load(z, mask, j, tau, zh)) m = fmaxf(m, zh);
-    }
-    m = block_max(m, sm);
-    if (threadIdx.x == 0) pmax[blockIdx.x] = m;
-}
-
-__device__ __forceinline__ float seg_max(const SelSeg& S, const float* pmax) {
-    float M = -INFINITY;
-    for (int p = 0; p < S.n_parts; ++p) M = fmaxf(M, pmax[S.first_part + p]);
-    return M;
-}
-
-__global__ void __launch_bounds__(kSelThreads) sel_sum_kernel(const float* z, const uint8_t* mask, float tau,
-                                                              const SelSeg* segs, const SelPart* parts,
-                                                              const float* pmax, long long* psum, long long* tsum) {
-    __shared__ long long sm[32];
-    const SelPart P = parts[blockIdx.x];
-    const float M = seg_max(segs[P.seg], pmax);
-    long long part = 0;
-    for (int t = 0; t < kSelTilesPerPart; ++t) {
-        const int64_t t0 = P.begin + (int64_t)t * kSelTile;
-        long long s = 0;
-        if (t0 < P.end && M > -INFINITY) {
+    const int tid = threadIdx.x;
+    const bool vec = (((uintptr_t)(z + P.begin)) & 15) == 0 &&
+                     (mask == nullptr || (((uintptr_t)(mask + P.begin)) & 3) == 0);
+    float v[4 * kSelGroups];
+    uint32_t mb[kSelGroups];
 #pragma unroll
-            for (int i = 0; i < kSelPerThread; ++i) {
-                const int64_t j = t0 + i * kSelThreads + threadIdx.x;
-                if (j < P.end) {
-                    float zh;
-                    const bool ok = sel_load(z, mask, j, tau, zh);
-                    s += sel_weight(zh, ok, M);
-                }
+    for (int g = 0; g < kSelGroups; ++g) {
+        const int64_t jj = P.begin + (int64_t)g * (4 * kSelThreads) + 4 * tid;
+        if (vec && jj + 3 < P.end) {
+            const float4 f = *(const float4*)(z + jj);
+            v[4 * g] = f.x;
+            v[4 * g + 1] = f.y;
+            v[4 * g + 2] = f.z;
+            v[4 * g + 3] = f.w;
+            mb[g] = mask ? *(const uint32_t*)(mask + jj) : 0x01010101u;
+        } else {
+            uint32_t m = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t j = jj + i;
+                v[4 * g + i] = j < P.end ? z[j] : -INFINITY;
+                m |= (j < P.end ? (mask ? (uint32_t)mask[j] : 1u) : 0u) << (8 * i);
             }
+            mb[g] = m;
         }
-        s = block_sum(s, sm);
-        if (threadIdx.x == 0) tsum[(size_t)blockIdx.x * kSelTilesPerPart + t] = s;
-        part += s;
     }
-    if (threadIdx.x == 0) psum[blockIdx.x] = part;
+    float m = -INFINITY;
+#pragma unroll
+    for (int g = 0; g < kSelGroups; ++g)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (sel_ok(v[4 * g + i], (mb[g] >> (8 * i)) & 0xFFu)) m = fmaxf(m, v[4 * g + i]);
+    const float mp = block_max(m, smf) * inv_tau;
+    long long part = 0;
+#pragma unroll
+    for (int k = 0; k < kSelTilesPerPart; ++k) {
+        long long sk = 0;
+        if (mp > -INFINITY) {
+#pragma unroll
+            for (int g = 2 * k; g < 2 * k + 2; ++g)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    sk += sel_weight(v[4 * g + i], sel_ok(v[4 * g + i], (mb[g] >> (8 * i)) & 0xFFu), inv_tau, mp);
+        }
+        sk = block_sum(sk, sml);
+        if (tid == 0) tsum[(size_t)blockIdx.x * kSelTilesPerPart + k] = sk;
+        part += sk;
+    }
+    if (tid == 0) {
+        pmax[blockIdx.x] = mp;
+        psum[blockIdx.x] = part;
+    }
+}
+
+// Exclusive prefix over the CTA of one int64 per thread (fixed order), and the total.
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sm, long long& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sm[warp] = incl;
+    __syncthreads();
+    long long before = 0, tot = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+        if (w < warp) before += sm[w];
+        tot += sm[w];
+    }
+    __syncthreads();
+    total = tot;
+    return before + incl - v;
+}
+
+// Integer weight of part p of a segment with maximum M: rn(S_p exp(m_p - M))
+// (exactly S_p when m_p = M).
+__device__ __forceinline__ long long part_weight(long long Sp, float mp, float M) {
+    if (Sp == 0 || !(mp > -INFINITY)) return 0;
+    return llrint((double)Sp * exp((double)mp - (double)M));
 }
 
 // One CTA per segment.
-__global__ void __launch_bounds__(kSelThreads) sel_pick_kernel(const float* z, const uint8_t* mask, float tau,
+__global__ void __launch_bounds__(kSelThreads) sel_pick_kernel(const float* z, const uint8_t* mask, float inv_tau,
                                                                const SelSeg* segs, const SelPart* parts,
                                                                const float* pmax, const long long* psum,
                                                                const long long* tsum, uint64_t seed, uint64_t ctr,
                                                                int64_t* out_index, float* out_logp) {
-    __shared__ long long s_thr[kSelThreads];
-    __shared__ int64_t s_pos;
-    __shared__ long long s_rest;
+    __shared__ float smf[32];
+    __shared__ long long sml[32];
+    __shared__ int64_t s_tile;
+    __shared__ long long s_rest, s_t;
+    __shared__ int s_part;
     const int s_id = blockIdx.x;
     const SelSeg S = segs[s_id];
-    const float M = seg_max(S, pmax);
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        long long W = 0;
-        for (int p = 0; p < S.n_parts; ++p) W += psum[S.first_part + p];
-        int64_t pos = -1;
-        long long rest = 0;
-        if (W > 0) {
-            // u = m 2^-53 from the segment's Philox block, t = floor(u W) exactly
-            uint32_t c0 = (uint32_t)ctr, c1 = (uint32_t)(ctr >> 32), c2 = (uint32_t)s_id, c3 = kSelStream;
-            philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-            const unsigned long long m = ((unsigned long long)c0 << 21) | (c1 >> 11);
-            const unsigned long long lo = m * (unsigned long long)W;
-            const unsigned long long hi = __umul64hi(m, (unsigned long long)W);
-            long long t = (long long)((hi << 11) | (lo >> 53));
-            // part, then tile, whose running sum first exceeds t
-            int p = 0;
-            while (p < S.n_parts - 1 && t >= psum[S.first_part + p]) t -= psum[S.first_part + p++];
-            const int gp = S.first_part + p;
-            int k = 0;
-            while (k < kSelTilesPerPart - 1 && t >= tsum[(size_t)gp * kSelTilesPerPart + k])
-                t -= tsum[(size_t)gp * kSelTilesPerPart + k++];
-            pos = parts[gp].begin + (int64_t)k * kSelTile;
-            rest = t;
+    const int np = S.n_parts;
+    // segment maximum and the parts' integer weights (thread tid owns the
+    // consecutive parts [c0, c1))
+    float m = -INFINITY;
+    for (int p = tid; p < np; p += kSelThreads) m = fmaxf(m, pmax[S.first_part + p]);
+    const float M = block_max(m, smf);
+    const int C = (np + kSelThreads - 1) / kSelThreads;
+    const int c0 = min(np, tid * C), c1 = min(np, c0 + C);
+    long long own = 0;
+    for (int p = c0; p < c1; ++p) own += part_weight(psum[S.first_part + p], pmax[S.first_part + p], M);
+    long long W = 0;
+    const long long excl = block_excl_scan(own, sml, W);
+    if (W <= 0) {
+        if (tid == 0) {
+            out_index[s_id] = -1;
+            out_logp[s_id] = NAN;
         }
-        s_pos = pos;
-        s_rest = rest;
-        out_logp[s_id] = W > 0 ? 0.f : NAN;
-    }
-    __syncthreads();
-    const int64_t tile0 = s_pos;
-    if (tile0 < 0) {
-        if (tid == 0) out_index[s_id] = -1;
         return;
     }
-    const int64_t seg_end = parts[S.first_part + S.n_parts - 1].end;
+    if (tid == 0) {
+        // u = m 2^-53 from the segment's Philox block, t = floor(u W) exactly
+        uint32_t x0 = (uint32_t)ctr, x1 = (uint32_t)(ctr >> 32), x2 = (uint32_t)s_id, x3 = kSelStream;
+        philox4x32_10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const unsigned long long u53 = ((unsigned long long)x0 << 21) | (x1 >> 11);
+        const unsigned __int128 prod = (unsigned __int128)u53 * (unsigned long long)W;
+        s_t = (long long)(prod >> 53);
+    }
+    __syncthreads();
+    const long long t = s_t;
+    if (t >= excl && t < excl + own) {
+        // this thread's parts hold t: the part, then t in the part's own units
+        long long r = t - excl;
+        int p = c0;
+        for (; p < c1 - 1; ++p) {
+            const long long w = part_weight(psum[S.first_part + p], pmax[S.first_part + p], M);
+            if (r < w) break;
+            r -= w;
+        }
+        const int gp = S.first_part + p;
+        const long long Sp = psum[gp];
+        const long long w = part_weight(Sp, pmax[gp], M);
+        long long ti = (long long)(((unsigned __int128)r * (unsigned long long)Sp) / (unsigned long long)w);
+        ti = min(ti, Sp - 1);
+        int k = 0;
+        while (k < kSelTilesPerPart - 1 && ti >= tsum[(size_t)gp * kSelTilesPerPart + k])
+            ti -= tsum[(size_t)gp * kSelTilesPerPart + k++];
+        s_part = gp;
+        s_tile = parts[gp].begin + (int64_t)k * kSelTile;
+        s_rest = ti;
+    }
+    __syncthreads();
+    const int gp = s_part;
+    const float mp = pmax[gp];
+    const int64_t part_end = parts[gp].end;
     // the tile's logits in order: thread i takes 8 consecutive ones
-    const int64_t j0 = tile0 + (int64_t)tid * kSelPerThread;
+    const int64_t j0 = s_tile + (int64_t)tid * kSelPerThread;
     long long q[kSelPerThread];
     float zq[kSelPerThread];
-    long long own = 0;
+    long long mine = 0;
 #pragma unroll
     for (int i = 0; i < kSelPerThread; ++i) {
         const int64_t j = j0 + i;
         q[i] = 0;
         zq[i] = 0.f;
-        if (j < seg_end) {
-            const bool ok = sel_load(z, mask, j, tau, zq[i]);
-            q[i] = sel_weight(zq[i], ok, M);
+        if (j < part_end) {
+            const float v = z[j];
+            const bool ok = sel_ok(v, mask ? (uint32_t)mask[j] : 1u);
+            zq[i] = v * inv_tau;
+            q[i] = sel_weight(v, ok, inv_tau, mp);
         }
-        own += q[i];
+        mine += q[i];
     }
-    s_thr[tid] = own;
-    __syncthreads();
-    if (tid == 0) {
-        // exclusive prefix over the 256 thread sums; the owner of t
-        long long t = s_rest;
-        int owner = 0;
-        while (owner < kSelThreads - 1 && t >= s_thr[owner]) t -= s_thr[owner++];
-        s_thr[0] = owner;
-        s_rest = t;
-    }
-    __syncthreads();
-    if (tid == (int)s_thr[0]) {
-        long long t = s_rest;
+    long long tile_total = 0;
+    const long long before = block_excl_scan(mine, sml, tile_total);
+    const long long r = s_rest;
+    if (r >= before && r < before + mine) {
+        long long rr = r - before;
         int i = 0;
-        while (i < kSelPerThread - 1 && t >= q[i]) t -= q[i++];
-        const int64_t j = j0 + i;
-        out_index[s_id] = j - S.begin;
-        long long W = 0;
-        for (int p = 0; p < S.n_parts; ++p) W += psum[S.first_part + p];
+        while (i < kSelPerThread - 1 && rr >= q[i]) rr -= q[i++];
+        out_index[s_id] = j0 + i - S.begin;
         out_logp[s_id] = (float)((double)(zq[i] - M) - log((double)W * 0x1p-32));
     }
 }
@@ -342,10 +399,10 @@ extern "C" akmc_status akmc_select_logits(const float* logits, const uint8_t* ma
     long long* psum = (long long*)(base + l.psum);
     long long* tsum = (long long*)(base + l.tsum);
     cudaStream_t st = (cudaStream_t)stream;
-    sel_max_kernel<<<n_parts, kSelThreads, 0, st>>>(logits, mask, tau, parts, pmax);
-    sel_sum_kernel<<<n_parts, kSelThreads, 0, st>>>(logits, mask, tau, segs, parts, pmax, psum, tsum);
-    sel_pick_kernel<<<n_seg, kSelThreads, 0, st>>>(logits, mask, tau, segs, parts, pmax, psum, tsum, seed, counter,
-                                                   out_index, out_logp);
+    const float inv_tau = 1.0f / tau;
+    sel_part_kernel<<<n_parts, kSelThreads, 0, st>>>(logits, mask, inv_tau, parts, pmax, psum, tsum);
+    sel_pick_kernel<<<n_seg, kSelThreads, 0, st>>>(logits, mask, inv_tau, segs, parts, pmax, psum, tsum, seed,
+                                                   counter, out_index, out_logp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sel_fail(AKMC_ECUDA, std::string("select kernels: ") + cudaGetErrorString(e));
     return AKMC_OK;
