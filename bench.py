@@ -54,10 +54,10 @@ EAM_BYTES_PER_EVENT = 145 * (1 + 4) + 2 + 78 * 4 * 2
 RATE_BYTES_PER_SITE = 5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per event of one
 # full-size step-kernel launch, from one ncu capture of
-# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (545 MB read +
-# 5.38 GB written for 2.56e8 events); valid only for the kernel source it was
+# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (536 MB read +
+# 5.36 GB written for 2.56e8 events); valid only for the kernel source it was
 # taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": "733a5b1e84a42960c7c76b6f51af629dbd9f2f6c", "bytes_per_event": 23.15}
+NCU_STEP_TRAFFIC = {"k_step_sha1": "def9523bf838cd29265b41eb81e212507f18818c", "bytes_per_event": 23.03}
 
 
 def _step_src_sha1():
@@ -336,7 +336,7 @@ def logit_select_leg(torch, dev, peak, peak_kind):
     select_logits(plan, logits, 1.0, 1, 0, mask)
     ts = [_time_region(lambda c=c: select_logits(plan, logits, 1.0, 1, c + 1, mask), torch) for c in range(5)]
     gbs = 5.0 * n_seg * per / min(ts) / 1e9
-    return {"bound": "hbm", "kernel": "akmc_select_logits (part max, part sums, search)", "achieved": gbs,
+    return {"bound": "hbm", "kernel": "akmc_select_logits (part pass, system search)", "achieved": gbs,
             "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
             "workload": "256 systems x 524288 logits (float32) + mask (uint8), 671 MB", "ms": 1e3 * min(ts)}
 

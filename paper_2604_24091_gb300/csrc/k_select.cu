@@ -118,11 +118,11 @@ __device__ __forceinline__ long long sel_weight(float v, bool ok, float inv_tau,
 // times 1/tau: multiplication by a positive constant keeps the order), and the
 // exact tile and part sums of q = rn(exp(z/tau - m_p) 2^32).  Tile k holds
 // groups 2k and 2k + 1.
-__global__ void __launch_bounds__(kSelThreads) sel_part_kernel(const float* z, const uint8_t* mask, float inv_tau,
+__global__ void __launch_bounds__(kSelThreads, 4) sel_part_kernel(const float* z, const uint8_t* mask, float inv_tau,
                                                                const SelPart* parts, float* pmax, long long* psum,
                                                                long long* tsum) {
     __shared__ float smf[32];
-    __shared__ long long sml[32];
+    __shared__ long long sml[kSelThreads / 32][kSelTilesPerPart];
     const SelPart P = parts[blockIdx.x];
     const int tid = threadIdx.x;
     const bool vec = (((uintptr_t)(z + P.begin)) & 15) == 0 &&
@@ -157,24 +157,36 @@ __global__ void __launch_bounds__(kSelThreads) sel_part_kernel(const float* z, c
         for (int i = 0; i < 4; ++i)
             if (sel_ok(v[4 * g + i], (mb[g] >> (8 * i)) & 0xFFu)) m = fmaxf(m, v[4 * g + i]);
     const float mp = block_max(m, smf) * inv_tau;
-    long long part = 0;
+    // the four tile sums, reduced together (warp shuffles, then one pass over the warps)
+    long long sk[kSelTilesPerPart];
 #pragma unroll
     for (int k = 0; k < kSelTilesPerPart; ++k) {
-        long long sk = 0;
+        sk[k] = 0;
         if (mp > -INFINITY) {
 #pragma unroll
             for (int g = 2 * k; g < 2 * k + 2; ++g)
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    sk += sel_weight(v[4 * g + i], sel_ok(v[4 * g + i], (mb[g] >> (8 * i)) & 0xFFu), inv_tau, mp);
+                    sk[k] += sel_weight(v[4 * g + i], sel_ok(v[4 * g + i], (mb[g] >> (8 * i)) & 0xFFu), inv_tau, mp);
         }
-        sk = block_sum(sk, sml);
-        if (tid == 0) tsum[(size_t)blockIdx.x * kSelTilesPerPart + k] = sk;
-        part += sk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], o);
     }
-    if (tid == 0) {
-        pmax[blockIdx.x] = mp;
-        psum[blockIdx.x] = part;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kSelTilesPerPart; ++k) sml[warp][k] = sk[k];
+    __syncthreads();
+    if (tid < kSelTilesPerPart) {
+        long long t = 0;
+        for (int w = 0; w < kSelThreads / 32; ++w) t += sml[w][tid];
+        tsum[(size_t)blockIdx.x * kSelTilesPerPart + tid] = t;
+        const long long p1 = t + __shfl_xor_sync(0xfu, t, 1);
+        const long long p2 = p1 + __shfl_xor_sync(0xfu, p1, 2);
+        if (tid == 0) {
+            pmax[blockIdx.x] = mp;
+            psum[blockIdx.x] = p2;
+        }
     }
 }
 
