@@ -144,9 +144,14 @@ __host__ __device__ inline int strip_slot(int TY, int L) { return TY * strip_rw(
 // floor((b + d) / 2) for b in {0,1}, d in [-4, 4]
 __device__ __forceinline__ int half_floor(int v) { return (v + 8) / 2 - 4; }
 
+// Entries of rows hr in [4, ty) reach only rows inside the strip and go to the
+// front of the list (count[0]); the others go to the back (count[1], list
+// index cap - 1 - i) and are scattered with a row check.
+__device__ __forceinline__ bool strip_inner(int hr, int ty) { return hr >= 4 && hr < ty; }
+
 template <bool VEC>
 __device__ __forceinline__ void strip_append(const uint8_t* sp, int L, int zp, int y0, int ty, uint4 pre,
-                                             int my_hr, int my_cx, uint32_t* list, int* count) {
+                                             int my_hr, int my_cx, uint32_t* list, int cap, int* count) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int M2 = 2 * L;
     if (VEC) {
@@ -163,25 +168,22 @@ __device__ __forceinline__ void strip_append(const uint8_t* sp, int L, int zp, i
                 M |= ((t | (t >> 7) | (t >> 14) | (t >> 21)) & 0xFu) << (4 * i);
             }
         }
-        const int c = __popc(M);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+        if (M) {
+            const int c = __popc(M);
+            const bool in = strip_inner(my_hr, ty);
+            const int at0 = atomicAdd(&count[in ? 0 : 1], c);
+            int i = 0;
+            while (M) {
+                const int j = __ffs(M) - 1;
+                M &= M - 1;
+                const uint32_t wj = j < 8 ? (j < 4 ? pre.x : pre.y) : (j < 12 ? pre.z : pre.w);
+                const uint32_t s = (wj >> (8 * (j & 3))) & 0xFFu;
+                const uint32_t en = (s > 7 ? 7u : s) | ((uint32_t)(16 * my_cx + j) << 3) | ((uint32_t)my_hr << 13);
+                list[in ? at0 + i : cap - 1 - (at0 + i)] = en;
+                ++i;
+            }
         }
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        int base = 0;
-        if (lane == 31 && tot) base = atomicAdd(count, tot);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int at = base + incl - c;
-        while (M) {
-            const int j = __ffs(M) - 1;
-            M &= M - 1;
-            const uint32_t wj = j < 8 ? (j < 4 ? pre.x : pre.y) : (j < 12 ? pre.z : pre.w);
-            const uint32_t s = (wj >> (8 * (j & 3))) & 0xFFu;
-            list[at++] = (s > 7 ? 7u : s) | ((uint32_t)(16 * my_cx + j) << 3) | ((uint32_t)my_hr << 13);
-        }
+        (void)lane;
     } else {
         // byte path (rows not 16-byte aligned): one byte per thread and pass
         const int n = (ty + 4) * M2;
@@ -196,13 +198,16 @@ __device__ __forceinline__ void strip_append(const uint8_t* sp, int L, int zp, i
                 y = y < 0 ? y + L : (y >= L ? y - L : y);
                 s = sp[((size_t)zp * L + y) * M2 + X];
             }
-            const bool hit = s != 0;
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(count, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (hit) list[base + __popc(m & ((1u << lane) - 1u))] =
-                         (s > 7 ? 7u : s) | ((uint32_t)X << 3) | ((uint32_t)hr << 13);
+            const bool hit = s != 0, in = strip_inner(hr, ty);
+            const unsigned mi = __ballot_sync(0xffffffffu, hit && in), me = __ballot_sync(0xffffffffu, hit && !in);
+            int bi = 0, be = 0;
+            if (lane == 0 && mi) bi = atomicAdd(&count[0], __popc(mi));
+            if (lane == 0 && me) be = atomicAdd(&count[1], __popc(me));
+            bi = __shfl_sync(0xffffffffu, bi, 0);
+            be = __shfl_sync(0xffffffffu, be, 0);
+            const uint32_t en = (s > 7 ? 7u : s) | ((uint32_t)X << 3) | ((uint32_t)hr << 13);
+            if (hit && in) list[bi + __popc(mi & ((1u << lane) - 1u))] = en;
+            if (hit && !in) list[cap - 1 - (be + __popc(me & ((1u << lane) - 1u)))] = en;
         }
     }
 }
@@ -328,7 +333,7 @@ __device__ void strip_body(const VoxelDev& V, const int4 it, int TY, int32_t* bu
     };
     uint4 pre = make_uint4(0, 0, 0, 0);
     load(0, pre);
-    if (tid < 2) counts[tid] = 0;
+    if (tid < 4) counts[tid] = 0;
     __syncthreads();
     const int n_src = tz + 4;
     int qb = -2;
@@ -336,12 +341,29 @@ __device__ void strip_body(const VoxelDev& V, const int4 it, int TY, int32_t* bu
         const uint4 cur = pre;
         if (rp + 1 < n_src) load(rp + 1, pre);
         uint32_t* list = lists + (rp & 1) * list_cap;
-        strip_append<VEC>(V.species, L, plane_of(rp), y0, ty, cur, my_hr, my_cx, list, &counts[rp & 1]);
+        int* cnt = counts + 2 * (rp & 1);
+        strip_append<VEC>(V.species, L, plane_of(rp), y0, ty, cur, my_hr, my_cx, list, list_cap, cnt);
         __syncthreads();
-        const int n = counts[rp & 1] * kLanesPerSite;
         const int pos = rp - qb;                      // 2 .. 5: targets at buffer planes pos-2 .. pos+2
-        for (int t = tid; t < n; t += kStripThreads) {
+        // entries of inner rows: every target row lies in the strip
+        const int ni = cnt[0] * kLanesPerSite;
+        for (int t = tid; t < ni; t += kStripThreads) {
             const uint32_t en = list[t / kLanesPerSite];
+            const int s = en & 7, X = (en >> 3) & 1023, hr = en >> 13;
+            const int u = pos * SLOT + (hr - 2) * RW + X + kRowPad - 16384;
+            const int32_t* cs = cq[s];
+            const bool b = X & 1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j == 7 && sub + kLanesPerSite * j >= kSph) break;
+                const uint32_t w = b ? P1[j] : P0[j];
+                atomicAdd(buf + (u + (int)(w & 0x7FFF)), cs[w >> 18]);
+            }
+        }
+        // entries of edge rows: row check
+        const int ne = cnt[1] * kLanesPerSite;
+        for (int t = tid; t < ne; t += kStripThreads) {
+            const uint32_t en = list[list_cap - 1 - t / kLanesPerSite];
             const int s = en & 7, X = (en >> 3) & 1023, hr = en >> 13;
             const int u = pos * SLOT + (hr - 2) * RW + X + kRowPad - 16384;
             const int hm = hr - 4;                    // target row hr + dyc - 2 = hm + (dyc + 2)
@@ -352,10 +374,10 @@ __device__ void strip_body(const VoxelDev& V, const int4 it, int TY, int32_t* bu
                 if (j == 7 && sub + kLanesPerSite * j >= kSph) break;
                 const uint32_t w = b ? P1[j] : P0[j];
                 if ((unsigned)(hm + (int)((w >> 15) & 7)) < (unsigned)ty)
-                    atomicAdd(buf + u + (int)(w & 0x7FFF), cs[w >> 18]);
+                    atomicAdd(buf + (u + (int)(w & 0x7FFF)), cs[w >> 18]);
             }
         }
-        if (tid == 0) counts[(rp + 1) & 1] = 0;
+        if (tid < 2) counts[2 * ((rp + 1) & 1) + tid] = 0;
         __syncthreads();
         if (pos == kShift + 1) {                      // buffer planes 0..3 complete
             strip_shift<VEC>(V, buf, SLOT, RW, ty, y0, z0, qb, tz, rho0);
@@ -374,7 +396,7 @@ __global__ void __launch_bounds__(kStripThreads) density_strip_kernel(const Voxe
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t s_cq[8][8];
     __shared__ int32_t s_sph[64];
-    __shared__ int s_count[2];
+    __shared__ int s_count[4];
     const int4 it = items[blockIdx.x];
     const int tid = threadIdx.x;
     if (tid < kSph) s_sph[tid] = tab->sph_off[tid];
