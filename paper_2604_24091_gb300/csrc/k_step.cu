@@ -979,8 +979,9 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
     const int dm0 = wdelta(0, omk, W), dm1 = wdelta(1, omk, W);
     const int mkk = S.mk[k];
     const EmbedC E = embed_consts(S);
-    // per-thread constants of the density update (threads 32 .. 32+115)
-    const int ut = tid - 32;
+    // per-thread constants of the density update: threads of the warps that do
+    // not share warp 0's SM sub-partition (warp % 4 != 0), in order
+    const int ut = (warp & 3) ? (warp - 1 - warp / 4) * 32 + lane : -1;
     const bool upd = MODE != 0 && ut >= 0 && ut < 2 * kSph;
     const int uside = upd && ut >= kSph;
     const int32_t uo = upd ? S.sph[uside ? ut - kSph : ut] : off_pack(0, 0, 0, 0);
