@@ -75,6 +75,7 @@ def lib():
                 "orc_hop_rate": (D, [P, I, I]),
                 "orc_rho_fixed": (ctypes.c_int64, [P, I]),
                 "orc_rho_all": (None, [P, P]),
+                "orc_step_sublattice": (I, [P, U64, ctypes.c_uint32, ctypes.c_int32, D, ctypes.c_int32, P]),
                 "orc_set_debug": (None, [P, I]),
                 "orc_debug_counts": (None, [P, P]),
                 "orc_tracer_r2": (D, [P]),
@@ -199,6 +200,16 @@ class Voxel:
 
     def rho_fixed(self, site):
         return int(self._lib.orc_rho_fixed(self._h, int(site)))
+
+    def step_sublattice(self, k0, n_supersteps, sector_cells, window, reverse=False):
+        """Synchronous sublattice supersteps k0 .. k0+n-1; returns the events made per superstep."""
+        ev = np.zeros(int(n_supersteps), np.uint64)
+        st = self._lib.orc_step_sublattice(self._h, int(k0), int(n_supersteps), int(sector_cells), float(window),
+                                           int(bool(reverse)), _ptr(ev))
+        if st == EINVAL:
+            raise ValueError("bad sublattice parameters")
+        self.status = st
+        return ev
 
     def rho_all(self):
         out = np.zeros(self.n_sites, np.int64)

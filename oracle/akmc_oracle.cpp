@@ -133,6 +133,7 @@ struct orc_voxel {
     double t_hi = 0, t_lo = 0;
     uint64_t n = 0;
     int status = ORC_OK;
+    double sl_T = 0;
     mutable int numeric = 0;
     // debug
     int debug = 0;
@@ -561,6 +562,116 @@ bool one_event(orc_voxel* v, int32_t* log_entry, double* dt_entry) {
     return true;
 }
 
+// ---- synchronous sublattice schedule (intra-voxel parallel AKMC) -----------------
+// The voxel is cut into sectors of S^3 cells, each into 8 octants of (S/2)^3.
+// Superstep k evolves octant k mod 8 (bit 0: x half, bit 1: y, bit 2: z) of
+// every sector; each active octant runs its own KMC over the vacancies that
+// lie in it at the start of the superstep, with its own clock starting at 0,
+// until the next event's time would pass the window T (that event is not
+// made); a vacancy that leaves the octant takes no further part in the
+// superstep.  The reads of an event reach 4 half units beyond its vacancy and
+// its writes 4 half units beyond the vacancy's start (hop 1 + cutoff sphere
+// 3), while active octants of one superstep are S + 1 half units apart, so
+// for S >= 8 no event of one octant reads or writes what another octant's
+// events touch and their order does not matter; this serial schedule takes
+// them in sector order.  One cycle of 8 supersteps evolves every region for
+// T (a first-order splitting of the voxel's master equation into octant
+// parts), so the voxel's clock advances by T/8 per superstep.
+void sl_uniforms(uint64_t seed, uint64_t uid, uint32_t i, uint32_t k, uint32_t sector, double* u1, double* u2) {
+    uint32_t ctr[4] = {i, k, sector, 0xC0000000u | ((uint32_t)uid & 0x3FFFFFFFu)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    philox(ctr, key, x);
+    uint64_t a = ((uint64_t)x[0] << 21) | (x[1] >> 11);
+    uint64_t b = ((uint64_t)x[2] << 21) | (x[3] >> 11);
+    *u1 = (double)a * 0x1p-53;
+    *u2 = (double)(b + 1) * 0x1p-53;
+}
+
+bool in_octant(const orc_voxel* v, int site, int S, int sx, int sy, int sz, int oct) {
+    int X, Y, Z;
+    coords_of(v, site, X, Y, Z);
+    const int x = X >> 1, y = Y >> 1, z = Z >> 1, h = S / 2;
+    const int lx = x - sx * S - (oct & 1) * h, ly = y - sy * S - ((oct >> 1) & 1) * h,
+              lz = z - sz * S - ((oct >> 2) & 1) * h;
+    return lx >= 0 && lx < h && ly >= 0 && ly < h && lz >= 0 && lz < h;
+}
+
+// The hop (slot, dir): swap, densities, displacement, tracers, refresh of every
+// affected vacancy (as in one_event).
+void apply_hop(orc_voxel* v, int slot, int dir) {
+    int w = v->pos[slot];
+    int dx, dy, dz;
+    dirvec(dir, dx, dy, dz);
+    int m = nbr(v, w, dx, dy, dz);
+    int A = v->sp[m];
+    v->sp[w] = (uint8_t)A;
+    v->sp[m] = (uint8_t)VAC;
+    v->pos[slot] = m;
+    v->disp[3 * slot + 0] += dx;
+    v->disp[3 * slot + 1] += dy;
+    v->disp[3 * slot + 2] += dz;
+    if (v->model == 1) {
+        const Shells& S = shells();
+        for (const Off& o : S.sph) v->rho[nbr(v, w, o.dx, o.dy, o.dz)] += v->fq[A][o.shell];
+        for (const Off& o : S.sph) v->rho[nbr(v, m, o.dx, o.dy, o.dz)] -= v->fq[A][o.shell];
+    }
+    if (v->debug & 8) {
+        for (int c = 0; c < 3; ++c) {
+            int d = c == 0 ? dx : (c == 1 ? dy : dz);
+            v->tdisp[3 * w + c] = v->tdisp[3 * m + c] - d;
+            v->tdisp[3 * m + c] = 0;
+        }
+    }
+    v->n++;
+    v->numeric = 0;
+    for (int q = 0; q < v->nv; ++q)
+        if (q == slot || affected(v, v->pos[q], w, m)) refresh_vacancy(v, q);
+    if (v->numeric) v->status = ORC_ENUMERIC;
+}
+
+uint64_t sl_octant(orc_voxel* v, uint32_t k, int S, int sid, int oct) {
+    const int ns = v->L / S;
+    const int sx = sid % ns, sy = (sid / ns) % ns, sz = sid / (ns * ns);
+    std::vector<int> act;
+    for (int q = 0; q < v->nv; ++q)
+        if (in_octant(v, v->pos[q], S, sx, sy, sz, oct)) act.push_back(q);
+    if (act.empty()) return 0;
+    std::vector<char> on(act.size(), 1);
+    int P = 1;
+    while (P < (int)act.size()) P <<= 1;
+    std::vector<double> tree(2 * P, 0.0);
+    double t = 0.0;
+    uint32_t i = 0;
+    uint64_t made = 0;
+    for (;;) {
+        if (v->status != ORC_OK) break;
+        std::fill(tree.begin(), tree.end(), 0.0);
+        for (size_t j = 0; j < act.size(); ++j)
+            tree[P + j] = on[j] ? vacancy_sum(&v->rate[8 * act[j]]) : 0.0;
+        for (int n = P - 1; n >= 1; --n) tree[n] = tree[2 * n] + tree[2 * n + 1];
+        const double R = tree[1];
+        if (!(R > 0.0)) break;
+        double u1, u2;
+        sl_uniforms(v->seed, v->uid, i, k, (uint32_t)sid, &u1, &u2);
+        const double dt = -std::log(u2) / R;
+        if (t + dt > v->sl_T) break;
+        double tt = u1 * R;
+        const int j = descend(tree.data(), P, tt);
+        const double* g = &v->rate[8 * act[j]];
+        double h[16];
+        for (int d = 0; d < 8; ++d) h[8 + d] = g[d];
+        for (int n = 7; n >= 1; --n) h[n] = h[2 * n] + h[2 * n + 1];
+        const int dir = descend(h, 8, tt);
+        apply_hop(v, act[j], dir);
+        if (!in_octant(v, v->pos[act[j]], S, sx, sy, sz, oct)) on[j] = 0;
+        t += dt;
+        ++i;
+        ++made;
+    }
+    return made;
+}
+
 int init_model(orc_voxel* v, const orc_model* m) {
     std::memcpy(v->eps1, m->eps1, sizeof v->eps1);
     std::memcpy(v->eps2, m->eps2, sizeof v->eps2);
@@ -713,6 +824,32 @@ int orc_step(orc_voxel* v, uint64_t n, int32_t* log, double* dt_log) {
     for (uint64_t i = 0; i < n; ++i) {
         if (v->status != ORC_OK) break;
         if (!one_event(v, log ? log + i : nullptr, dt_log ? dt_log + i : nullptr)) break;
+    }
+    return v->status;
+}
+
+int orc_step_sublattice(orc_voxel* v, uint64_t k0, uint32_t n_supersteps, int32_t S, double T, int32_t reverse,
+                        uint64_t* events) {
+    if (S < 8 || S % 2 || v->L % S || !(T > 0.0)) return ORC_EINVAL;
+    const int ns = v->L / S, n_sec = ns * ns * ns;
+    v->sl_T = T;
+    for (uint32_t st = 0; st < n_supersteps; ++st) {
+        if (v->status != ORC_OK) break;
+        const uint32_t k = (uint32_t)(k0 + st);
+        const int oct = (int)(k % 8);
+        uint64_t made = 0;
+        for (int idx = 0; idx < n_sec; ++idx) {
+            const int sid = reverse ? n_sec - 1 - idx : idx;
+            made += sl_octant(v, k, S, sid, oct);
+        }
+        const double dt = T * 0.125;
+        double s2 = v->t_hi + dt;
+        if (std::fabs(v->t_hi) >= std::fabs(dt))
+            v->t_lo += (v->t_hi - s2) + dt;
+        else
+            v->t_lo += (dt - s2) + v->t_hi;
+        v->t_hi = s2;
+        if (events) events[st] = made;
     }
     return v->status;
 }

@@ -61,6 +61,13 @@ int orc_load(orc_voxel* v, const uint8_t* species, const int32_t* vac_pos, int32
  * 8*slot+dir and dt_log the residence time of the state before each event
  * (both nullable, capacity n). */
 int orc_step(orc_voxel* v, uint64_t n, int32_t* log, double* dt_log);
+/* Synchronous sublattice schedule: n_supersteps supersteps k0, k0+1, ...; sectors
+ * of S^3 cells (S even, >= 8, dividing L), window T seconds per octant (the
+ * clock advances T/8 per superstep); reverse != 0 takes
+ * the sectors of a superstep in descending order (the result must not change).
+ * events[st] (nullable) gets the events made in superstep st. */
+int orc_step_sublattice(orc_voxel* v, uint64_t k0, uint32_t n_supersteps, int32_t S, double T, int32_t reverse,
+                        uint64_t* events);
 int orc_get(const orc_voxel* v, uint8_t* species, int32_t* vac_pos, int32_t* vac_disp,
             double* rates, double* dE, double* t_hi, double* t_lo, uint64_t* n_events);
 int32_t orc_n_sites(const orc_voxel* v);
