@@ -151,6 +151,28 @@ akmc_status akmc_step_n(akmc_batch* batch, const uint64_t* n_events, akmc_stream
 akmc_status akmc_set_targets(akmc_batch* batch, const uint64_t* n_events, akmc_stream stream);
 akmc_status akmc_launch_step(akmc_batch* batch, akmc_stream stream);
 
+/* Synchronous sublattice supersteps of one voxel (intra-voxel parallel AKMC,
+ * the synchronous form of the sublattice scheme of Sec. 3.2.2).  The voxel is
+ * cut into sectors of sector_cells^3 cells (sector_cells even, >= 8, dividing
+ * L) and each sector into 8 octants of (sector_cells/2)^3 cells.  Superstep
+ * k = superstep0, ..., superstep0 + n_supersteps - 1 evolves octant k mod 8
+ * (bit 0: upper half in x, bit 1: y, bit 2: z) of every sector at once: each
+ * runs residence-time KMC over the vacancies inside it at the superstep start,
+ * with a clock from 0, up to (not including) the first event past window_s
+ * seconds; a vacancy that leaves its octant takes no further part in the
+ * superstep.  Event i of sector c = (cz (L/Sc) + cy) (L/Sc) + cx in superstep
+ * k draws Philox(seed, (i, k, c, 0xC0000000 | uid & 0x3fffffff)).  The voxel
+ * clock advances by window_s / 8 per superstep (a cycle of 8 supersteps
+ * evolves every region for window_s; Neumaier-compensated), the event
+ * counter by the events made; there is no event log.  Sectors of a superstep
+ * are independent (events reach 4 half units, active octants are
+ * sector_cells + 1 apart), so the result does not depend on their order.  The
+ * voxel's rates and tree are rebuilt after the last superstep.  Stream-ordered,
+ * no synchronisation; per-voxel status as for akmc_step_n.  AKMC_EINVAL for a
+ * bad voxel index, sector size or window (not finite or <= 0). */
+akmc_status akmc_step_sublattice(akmc_batch* batch, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
+                                 int32_t sector_cells, double window_s, akmc_stream stream);
+
 /* Re-seed n voxel slots in place with new descriptors (continuous batching:
  * a finished request's slot takes the next request).  Each new descriptor
  * must keep the slot's L, n_vac, model and precision; T, composition, seed

@@ -263,7 +263,7 @@ size_t al(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     size_t status = 0, model = 0, tab = 0, vox = 0, targets = 0, order = 0, queue = 0, hist = 0;
     size_t phi_raw = 0, f_raw = 0, F_raw = 0, Fd = 0, Ff = 0, Fq = 0, items = 0;
-    size_t labels = 0, sizes = 0, total = 0;
+    size_t labels = 0, sizes = 0, total = 0, ident = 0;
     std::vector<size_t> species, rho, pos, disp, rates, dE, hop, tree, log, etab;
     size_t state_begin = 0, state_end = 0, io = 0, reset_list = 0, reset_items = 0;
     size_t b_species = 0, b_pos = 0, b_disp = 0, tot_N = 0, tot_nv = 0;
@@ -289,6 +289,7 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
     Lo.vox = take(sizeof(VoxelDev) * n);
     Lo.targets = take(sizeof(uint64_t) * n + sizeof(int32_t) * n);   // targets then order
     Lo.order = Lo.targets + sizeof(uint64_t) * n;
+    Lo.ident = take(sizeof(int32_t) * n);   // 0, 1, ..., n-1: single-voxel kernel lists
     if (has_eam) {
         Lo.phi_raw = take(sizeof(double) * 20 * m->n_r);
         Lo.f_raw = take(sizeof(double) * 8 * m->n_r);
@@ -579,6 +580,9 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
                              cudaMemcpyHostToDevice, s));
     AKMC_TRY(cudaMemcpyAsync(b->base + lo.targets, b->staging, (sizeof(uint64_t) + sizeof(int32_t)) * n,
                              cudaMemcpyHostToDevice, s));
+    std::vector<int32_t> ident(n);
+    for (int32_t v = 0; v < n; ++v) ident[v] = v;
+    AKMC_TRY(cudaMemcpyAsync(b->base + lo.ident, ident.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     AKMC_TRY(cudaEventRecord(b->staging_done[0], s));
     b->staging_used[0] = true;
     b->stage = 1;
@@ -670,6 +674,35 @@ akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream str
     akmc_status st = akmc_set_targets(b, n_events, stream);
     if (st != AKMC_OK) return st;
     return akmc_launch_step(b, stream);
+}
+
+akmc_status akmc_step_sublattice(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
+                                 int32_t sector_cells, double window_s, akmc_stream stream) {
+    if (!b) return fail(AKMC_EINVAL, "batch is NULL");
+    if (voxel < 0 || voxel >= b->n) return fail(AKMC_EINVAL, "voxel %d out of range", voxel);
+    const int L = b->desc[voxel].L, Sc = sector_cells;
+    if (Sc < 8 || Sc % 2 || L % Sc)
+        return fail(AKMC_EINVAL, "sector_cells %d must be even, >= 8 and divide L = %d", Sc, L);
+    if (!(window_s > 0.0) || !std::isfinite(window_s)) return fail(AKMC_EINVAL, "window must be positive and finite");
+    if (n_supersteps == 0) return AKMC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->dirty) {
+        akmc_status st = rebuild(b, s);
+        if (st != AKMC_OK) return st;
+    }
+    const BatchArgs a = b->args();
+    cudaError_t e = sl_prepare(a);
+    if (e != cudaSuccess) return fail(AKMC_ECUDA, "sublattice kernel attribute: %s", cudaGetErrorString(e));
+    const int ns = L / Sc;
+    for (uint32_t i = 0; i < n_supersteps; ++i) {
+        e = launch_sublattice(a, voxel, (uint32_t)(superstep0 + i), Sc, ns * ns * ns, window_s, s);
+        if (e != cudaSuccess) return fail(AKMC_ECUDA, "sublattice kernel: %s", cudaGetErrorString(e));
+    }
+    // the supersteps keep lattice, densities, positions, clock and counter; the
+    // voxel's rates and tree are rebuilt from the new lattice
+    e = launch_rebuild(a, 8, (const int32_t*)(b->base + b->lo.ident) + voxel, 1, s);
+    if (e != cudaSuccess) return fail(AKMC_ECUDA, "rebuild kernel: %s", cudaGetErrorString(e));
+    return AKMC_OK;
 }
 
 akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_voxel_desc* descs, int32_t n,

@@ -27,6 +27,12 @@ cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, cons
 cudaError_t launch_step(const BatchArgs& a, int warps, int grid, cudaStream_t st);
 cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, int n_list, cudaStream_t st);
 int step_occupancy(int warps, int max_nv, int max_P, int win);
+// Synchronous sublattice supersteps of one voxel: sl_prepare sets the kernel's
+// shared-memory limit (once per call sequence, outside any capture);
+// launch_sublattice runs superstep k over n_sectors = (L/sector_cells)^3 CTAs.
+cudaError_t sl_prepare(const BatchArgs& a);
+cudaError_t launch_sublattice(const BatchArgs& a, int vid, uint32_t k, int sector_cells, int n_sectors,
+                              double window, cudaStream_t st);
 
 const Tables& host_tables();   // stencil tables built on the host
 void set_last_error(const char* msg);   // text returned by akmc_last_error() on this thread

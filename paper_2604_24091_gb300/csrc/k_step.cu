@@ -91,6 +91,11 @@ struct __align__(16) StepShared {
     int32_t pA, pw, pm, pwb, pmb;     // hop whose density change is pending: atom, window sites, parities
     int32_t pwX, pwY, pwZ, pmX, pmY, pmZ;
     double nx1, nx2;                  // uniforms of the event after the next one
+    // sublattice superstep (see sl_kernel): counter words of the uniforms,
+    // octant bounds (cells) and the octant's clock and window
+    int32_t sl_on, sl_k, sl_sid, sl_n;
+    int32_t sl_x0, sl_y0, sl_z0, sl_h;
+    double sl_t, sl_T;
 };
 
 struct Dyn {
@@ -109,13 +114,15 @@ struct Dyn {
     uint8_t* wsp;     // window species (single-vacancy path; padded layout, see widx)
     int32_t* wrho;    // window densities (same layout)
     int32_t* dprev;   // window path: density change of the last hop, [8 dirs][4 atoms][145 read-set sites]
+    int32_t* gslot;   // sublattice superstep: voxel slot of each local vacancy
+    int32_t* on;      // sublattice superstep: local vacancy still in the active octant
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Offsets of the dynamic shared-memory arrays (16-byte aligned).
 struct DynLayout {
-    size_t off[15];
+    size_t off[17];
     size_t total;
 };
 
@@ -123,17 +130,18 @@ __host__ __device__ inline int win_sites(int W);
 
 __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) {
     const size_t nw = win > 0 ? (size_t)win_sites(win) : 0;
-    const size_t sz[15] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
+    const size_t sz[17] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
                            sizeof(double) * 8 * max_nv, sizeof(double) * 8 * max_nv,
                            sizeof(double) * kEtab,      sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * 3 * max_nv,
                            sizeof(int32_t) * max_nv,    (size_t)8 * max_nv,
                            nw,                          sizeof(int32_t) * nw,
-                           win > 0 ? sizeof(int32_t) * kEamU * 32 : 0};
+                           win > 0 ? sizeof(int32_t) * kEamU * 32 : 0,
+                           sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv};
     DynLayout l;
     size_t o = 0;
-    for (int i = 0; i < 15; ++i) {
+    for (int i = 0; i < 17; ++i) {
         l.off[i] = o;
         o = align16(o + sz[i]);
     }
@@ -159,6 +167,8 @@ __device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P,
     d.wsp = win > 0 ? (uint8_t*)(base + l.off[12]) : nullptr;
     d.wrho = win > 0 ? (int32_t*)(base + l.off[13]) : nullptr;
     d.dprev = win > 0 ? (int32_t*)(base + l.off[14]) : nullptr;
+    d.gslot = (int32_t*)(base + l.off[15]);
+    d.on = (int32_t*)(base + l.off[16]);
     return d;
 }
 
@@ -197,6 +207,7 @@ __device__ void load_model(StepShared& S, const ModelDev* M) {
         S.inv_knot_f = (float)M->inv_knot;
         S.cur_model = -1;
         S.cur_small = -1;
+        S.sl_on = 0;
     }
 }
 
@@ -343,10 +354,18 @@ __device__ __forceinline__ double u53_to_double(uint64_t a) {
     return __longlong_as_double((long long)(((uint64_t)(e - 53 + 1023) << 52) | mant));
 }
 
+// Regular events: counter (n_lo, n_hi, uid_lo, uid_hi & 0x7fffffff).  Event i of
+// a sublattice superstep k in sector c: counter (i, k, c, 0xC0000000 | uid_lo
+// & 0x3fffffff) -- the top bits keep the two families of counters disjoint.
 __device__ __forceinline__ void next_uniforms(StepShared& S) {
     const uint64_t n = S.n, uid = S.v.uid, seed = S.v.seed;
     uint32_t c0 = (uint32_t)n, c1 = (uint32_t)(n >> 32), c2 = (uint32_t)uid,
              c3 = (uint32_t)(uid >> 32) & 0x7fffffffu;
+    if (S.sl_on) {
+        c1 = (uint32_t)S.sl_k;
+        c2 = (uint32_t)S.sl_sid;
+        c3 = 0xC0000000u | ((uint32_t)uid & 0x3FFFFFFFu);
+    }
     philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
     S.nu1 = u53_to_double(((uint64_t)c0 << 21) | (c1 >> 11));
     S.nu2 = u53_to_double((((uint64_t)c2 << 21) | (c3 >> 11)) + 1);
@@ -1284,6 +1303,218 @@ __global__ void __launch_bounds__(NW * 32) step_kernel(BatchArgs a) {
     }
 }
 
+// ---- synchronous sublattice superstep (intra-voxel parallel AKMC) ----------
+// The voxel is cut into sectors of Sc^3 cells and each sector into 8 octants of
+// (Sc/2)^3 cells.  Superstep k evolves octant k mod 8 (bit 0: upper half in x,
+// bit 1: y, bit 2: z) of every sector, one CTA per sector: a local KMC over the
+// vacancies inside the octant at the superstep start, with a local clock from
+// 0, stopping before the first event whose time would pass the window T; a
+// vacancy that leaves the octant drops out (rate 0) for the rest of the
+// superstep.  An event reads at most 4 half units beyond its vacancy and
+// writes at most 4 half units beyond its start site (hop 1 + cutoff sphere 3),
+// while active octants are Sc + 1 half units apart, so for Sc >= 8 the CTAs of
+// one superstep touch disjoint sites and need no synchronisation; kernel
+// boundaries order the supersteps.  A cycle of 8 supersteps evolves every
+// region for T (first-order splitting of the master equation into octant
+// parts): the voxel clock advances by T/8 per superstep.
+
+__device__ __forceinline__ bool sl_inside(const StepShared& S, int X, int Y, int Z) {
+    const int x = (X >> 1) - S.sl_x0, y = (Y >> 1) - S.sl_y0, z = (Z >> 1) - S.sl_z0, h = S.sl_h;
+    return (unsigned)x < (unsigned)h && (unsigned)y < (unsigned)h && (unsigned)z < (unsigned)h;
+}
+
+// Time step and window test, then (a6)/(a7) as in the regular path; executed by
+// thread 0.  Returns false when no active vacancy has a positive rate, when
+// the next event would pass the window, or on a numeric error.
+__device__ __forceinline__ bool sl_select(StepShared& S, const Dyn& D) {
+    if (S.numeric) {
+        S.v.status = kENUMERIC;
+        return false;
+    }
+    const double R = D.tree[1];
+    if (!(__double_as_longlong(R) > 0)) return false;
+    const double dt = -log(S.nu2) / R;
+    const double t = S.sl_t + dt;
+    if (t > S.sl_T) return false;
+    S.sl_t = t;
+    const bool ok = select_and_swap(S, D);
+    S.ccount = 0;   // the voxel clock does not take the octant's time steps
+    return ok;
+}
+
+// Events of one active octant (the loop of run_events with the window test,
+// and only the vacancies still inside the octant in the rate tree).
+template <int NW, int MODE>
+__device__ void run_events_sl(StepShared& S, const Dyn& D) {
+    const int tid = threadIdx.x;
+    const int L = S.v.L, M2 = 2 * L;
+    constexpr int reach = MODE != 0 ? 8 : 4;
+    const bool fast = S.v.nv == 1;
+    if (fast) {
+        phase_prefetch<NW, MODE>(S, D, 0);
+        __syncthreads();
+    }
+    for (;;) {
+        if (tid == 0) S.stop = !sl_select(S, D);
+        __syncthreads();
+        if (S.stop) break;
+        if (fast) {
+            phase_fill<NW, MODE>(S);
+            __syncthreads();
+        } else {
+            for (int q = tid; q < S.v.nv; q += NW * 32) {
+                if (q == S.slot || !D.on[q]) continue;
+                int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
+                ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
+                ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
+                ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
+                if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach)
+                    D.aff[atomicAdd(&S.n_aff, 1)] = q;
+            }
+            phase_gather<NW, MODE>(S, D, S.slot, true);
+            __syncthreads();
+            if (MODE == 1) {
+                phase_site_embed<NW>(S);
+                __syncthreads();
+            }
+        }
+        phase_terms<NW, MODE>(S, true);
+        __syncthreads();
+        if (tid < 32) {
+            phase_rates<MODE>(S, D, S.slot);
+            if (tid == 0) {
+                const int q = S.slot;
+                if (!sl_inside(S, D.X[q], D.Y[q], D.Z[q])) {
+                    D.on[q] = 0;
+                    const int P = S.v.P;
+                    D.tree[P + q] = 0.0;
+                    for (int i = (P + q) >> 1; i >= 1; i >>= 1) D.tree[i] = D.tree[2 * i] + D.tree[2 * i + 1];
+                }
+            }
+        }
+        if (fast) phase_prefetch<NW, MODE>(S, D, NW > 1 ? 32 : 0);
+        const int n_aff = fast ? 0 : S.n_aff;
+        if (n_aff > 0) {
+            __syncthreads();
+            for (int i = 0; i < n_aff; ++i) refresh_full<NW, MODE>(S, D, D.aff[i]);
+        }
+    }
+    __syncthreads();
+}
+
+// One superstep k of voxel `vid`, one CTA per sector (grid (L/Sc)^3).
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint32_t k, int Sc, double T) {
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    __shared__ StepShared S;
+    constexpr int NT = NW * 32;
+    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
+    const int tid = threadIdx.x, sid = blockIdx.x;
+    VoxelDev* gv = &a.vox[vid];
+    load_model<NW>(S, a.model);
+    if (tid == 0) {
+        S.v = *gv;
+        if (sid == 0 && S.v.status == kOK) {   // the voxel clock: T/8 per superstep, compensated
+            const double dt = T * 0.125, hi = S.v.t_hi + dt;
+            double lo = S.v.t_lo;
+            if (fabs(S.v.t_hi) >= fabs(dt))
+                lo += (S.v.t_hi - hi) + dt;
+            else
+                lo += (dt - hi) + S.v.t_hi;
+            gv->t_hi = hi;
+            gv->t_lo = lo;
+        }
+        const int ns = S.v.L / Sc, h = Sc / 2, oct = (int)(k & 7u);
+        S.sl_h = h;
+        S.sl_x0 = (sid % ns) * Sc + (oct & 1) * h;
+        S.sl_y0 = ((sid / ns) % ns) * Sc + ((oct >> 1) & 1) * h;
+        S.sl_z0 = (sid / (ns * ns)) * Sc + ((oct >> 2) & 1) * h;
+    }
+    __syncthreads();
+    if (S.v.status != kOK) return;   // uniform
+    // the active vacancies, in slot order
+    if (tid < 32) {
+        const int L = S.v.L, nv = S.v.nv;
+        int n = 0;
+        for (int b = 0; b < nv; b += 32) {
+            const int q = b + tid;
+            bool in = false;
+            if (q < nv) {
+                const int s = S.v.vac_pos[q], c = s >> 1, bit = s & 1;
+                in = sl_inside(S, 2 * (c % L) + bit, 2 * ((c / L) % L) + bit, 2 * (c / (L * L)) + bit);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (in) D.gslot[n + __popc(m & ((1u << tid) - 1u))] = q;
+            n += __popc(m);
+        }
+        if (tid == 0) S.sl_n = n;
+    }
+    __syncthreads();
+    const int n_act = S.sl_n;
+    if (n_act == 0) return;   // uniform
+    load_tables<NW>(S, a.tab, S.v.model, 0);
+    int P = 1;
+    while (P < n_act) P <<= 1;
+    const int L = S.v.L;
+    for (int j = tid; j < n_act; j += NT) {
+        const int q = D.gslot[j], s = S.v.vac_pos[q], c = s >> 1, bit = s & 1;
+        D.pos[j] = s;
+        D.X[j] = 2 * (c % L) + bit;
+        D.Y[j] = 2 * ((c / L) % L) + bit;
+        D.Z[j] = 2 * (c / (L * L)) + bit;
+        D.disp[3 * j + 0] = S.v.vac_disp[3 * q + 0];
+        D.disp[3 * j + 1] = S.v.vac_disp[3 * q + 1];
+        D.disp[3 * j + 2] = S.v.vac_disp[3 * q + 2];
+        D.on[j] = 1;
+    }
+    for (int i = tid; i < 2 * P; i += NT) D.tree[i] = 0.0;
+    for (int i = tid; i < kEtab; i += NT) D.etab[i] = S.v.etab[i];
+    __syncthreads();
+    if (tid == 0) {
+        S.v.nv = n_act;
+        S.v.P = P;
+        S.v.log_cap = 0;
+        S.sl_on = 1;
+        S.sl_k = (int32_t)k;
+        S.sl_sid = sid;
+        S.sl_t = 0.0;
+        S.sl_T = T;
+        S.n = 0;
+        S.stop = 0;
+        S.numeric = 0;
+        S.ccount = 0;
+        S.n_aff = 0;
+        next_uniforms(S);
+    }
+    __syncthreads();
+    const int mode = S.v.model == 0 ? 0 : (S.v.precision == 1 ? 1 : 2);
+    for (int j = 0; j < n_act; ++j) {
+        if (mode == 0)
+            refresh_full<NW, 0>(S, D, j);
+        else if (mode == 1)
+            refresh_full<NW, 1>(S, D, j);
+        else
+            refresh_full<NW, 2>(S, D, j);
+    }
+    if (mode == 0)
+        run_events_sl<NW, 0>(S, D);
+    else if (mode == 1)
+        run_events_sl<NW, 1>(S, D);
+    else
+        run_events_sl<NW, 2>(S, D);
+    for (int j = tid; j < n_act; j += NT) {
+        const int q = D.gslot[j];
+        S.v.vac_pos[q] = D.pos[j];
+        S.v.vac_disp[3 * q + 0] = D.disp[3 * j + 0];
+        S.v.vac_disp[3 * q + 1] = D.disp[3 * j + 1];
+        S.v.vac_disp[3 * q + 2] = D.disp[3 * j + 2];
+    }
+    if (tid == 0) {
+        if (S.n) atomicAdd((unsigned long long*)&gv->n_events, (unsigned long long)S.n);
+        if (S.v.status != kOK) atomicCAS(&gv->status, kOK, S.v.status);
+    }
+}
+
 // Full rebuild of one voxel per CTA: every vacancy's rates, then the tree
 // (leaf path updates in slot order leave every node = left + right of its
 // final children).
@@ -1381,6 +1612,16 @@ cudaError_t launch_rebuild(const BatchArgs& a, int warps, const int32_t* list, i
 #undef AKMC_CASE
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t sl_prepare(const BatchArgs& a) {
+    return set_smem<8>((const void*)sl_kernel<8>, step_dyn_smem(a.max_nv, a.max_P, 0));
+}
+
+cudaError_t launch_sublattice(const BatchArgs& a, int vid, uint32_t k, int sector_cells, int n_sectors,
+                              double window, cudaStream_t st) {
+    sl_kernel<8><<<n_sectors, 256, step_dyn_smem(a.max_nv, a.max_P, 0), st>>>(a, vid, k, sector_cells, window);
     return cudaGetLastError();
 }
 
