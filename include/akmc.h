@@ -173,6 +173,21 @@ akmc_status akmc_launch_step(akmc_batch* batch, akmc_stream stream);
 akmc_status akmc_step_sublattice(akmc_batch* batch, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
                                  int32_t sector_cells, double window_s, akmc_stream stream);
 
+/* The same supersteps with local readiness instead of a global barrier (the
+ * asynchronous sublattice scheme of Sec. 3.2.2): one cooperative launch runs
+ * all n_supersteps; each sector starts superstep k as soon as its 26
+ * neighbouring sectors have finished superstep k - 1 (per-sector counters in
+ * the workspace), so distant sectors run different supersteps at the same
+ * time.  Neighbouring sectors never run different supersteps concurrently,
+ * hence the result is identical to akmc_step_sublattice's (same lattice,
+ * positions, counts, clock).  Each readiness wait is bounded (a few
+ * seconds); on expiry the voxel's status becomes AKMC_ETIMEOUT.  Arguments,
+ * errors and stream semantics as for akmc_step_sublattice; the superstep
+ * index is taken modulo 2^32 in both. */
+akmc_status akmc_step_sublattice_async(akmc_batch* batch, int32_t voxel, uint64_t superstep0,
+                                       uint32_t n_supersteps, int32_t sector_cells, double window_s,
+                                       akmc_stream stream);
+
 /* Re-seed n voxel slots in place with new descriptors (continuous batching:
  * a finished request's slot takes the next request).  Each new descriptor
  * must keep the slot's L, n_vac, model and precision; T, composition, seed

@@ -69,6 +69,7 @@ def load_library():
             "akmc_reset_voxels": (I32, [P, P, P, I32, P]),
             "akmc_step_n": (I32, [P, P, P]),
             "akmc_step_sublattice": (I32, [P, I32, U64, ctypes.c_uint32, I32, ctypes.c_double, P]),
+            "akmc_step_sublattice_async": (I32, [P, I32, U64, ctypes.c_uint32, I32, ctypes.c_double, P]),
             "akmc_read_state": (I32, [P, I32, ctypes.POINTER(StateC), P]),
             "akmc_load_state": (I32, [P, I32, P, P, ctypes.c_double, ctypes.c_double, U64, P]),
             "akmc_sync_status": (I32, [P, P, P]),
@@ -217,10 +218,13 @@ class Batch:
         arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))
         _check(self._lib.akmc_step_n(self._h, _ptr(arr), _stream_ptr(stream)))
 
-    def step_sublattice(self, voxel, superstep0, n_supersteps, sector_cells, window, stream=None):
-        """Synchronous sublattice supersteps superstep0 .. superstep0+n-1 of one voxel."""
-        _check(self._lib.akmc_step_sublattice(self._h, int(voxel), int(superstep0), int(n_supersteps),
-                                              int(sector_cells), float(window), _stream_ptr(stream)))
+    def step_sublattice(self, voxel, superstep0, n_supersteps, sector_cells, window, asynchronous=False,
+                        stream=None):
+        """Sublattice supersteps superstep0 .. superstep0+n-1 of one voxel: one launch per
+        superstep, or (asynchronous=True) one launch with per-sector readiness."""
+        fn = self._lib.akmc_step_sublattice_async if asynchronous else self._lib.akmc_step_sublattice
+        _check(fn(self._h, int(voxel), int(superstep0), int(n_supersteps), int(sector_cells), float(window),
+                  _stream_ptr(stream)))
 
     def set_targets(self, n_events, stream=None):
         arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))

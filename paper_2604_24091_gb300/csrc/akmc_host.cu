@@ -263,7 +263,8 @@ size_t al(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     size_t status = 0, model = 0, tab = 0, vox = 0, targets = 0, order = 0, queue = 0, hist = 0;
     size_t phi_raw = 0, f_raw = 0, F_raw = 0, Fd = 0, Ff = 0, Fq = 0, items = 0;
-    size_t labels = 0, sizes = 0, total = 0, ident = 0;
+    size_t labels = 0, sizes = 0, total = 0, ident = 0, sl_done = 0;
+    int sl_max_sectors = 0;
     std::vector<size_t> species, rho, pos, disp, rates, dE, hop, tree, log, etab;
     size_t state_begin = 0, state_end = 0, io = 0, reset_list = 0, reset_items = 0;
     size_t b_species = 0, b_pos = 0, b_disp = 0, tot_N = 0, tot_nv = 0;
@@ -290,6 +291,11 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
     Lo.targets = take(sizeof(uint64_t) * n + sizeof(int32_t) * n);   // targets then order
     Lo.order = Lo.targets + sizeof(uint64_t) * n;
     Lo.ident = take(sizeof(int32_t) * n);   // 0, 1, ..., n-1: single-voxel kernel lists
+    for (int32_t v = 0; v < n; ++v) {
+        const int ns = d[v].L / 8;
+        Lo.sl_max_sectors = std::max(Lo.sl_max_sectors, ns * ns * ns);
+    }
+    Lo.sl_done = take(sizeof(int32_t) * (4 + (size_t)Lo.sl_max_sectors));   // abort word, then done[]
     if (has_eam) {
         Lo.phi_raw = take(sizeof(double) * 20 * m->n_r);
         Lo.f_raw = take(sizeof(double) * 8 * m->n_r);
@@ -676,14 +682,48 @@ akmc_status akmc_step_n(akmc_batch* b, const uint64_t* n_events, akmc_stream str
     return akmc_launch_step(b, stream);
 }
 
-akmc_status akmc_step_sublattice(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
-                                 int32_t sector_cells, double window_s, akmc_stream stream) {
+namespace {
+akmc_status sl_check(akmc_batch* b, int32_t voxel, int32_t Sc, double window_s) {
     if (!b) return fail(AKMC_EINVAL, "batch is NULL");
     if (voxel < 0 || voxel >= b->n) return fail(AKMC_EINVAL, "voxel %d out of range", voxel);
-    const int L = b->desc[voxel].L, Sc = sector_cells;
+    const int L = b->desc[voxel].L;
     if (Sc < 8 || Sc % 2 || L % Sc)
         return fail(AKMC_EINVAL, "sector_cells %d must be even, >= 8 and divide L = %d", Sc, L);
     if (!(window_s > 0.0) || !std::isfinite(window_s)) return fail(AKMC_EINVAL, "window must be positive and finite");
+    return AKMC_OK;
+}
+}  // namespace
+
+akmc_status akmc_step_sublattice_async(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
+                                       int32_t sector_cells, double window_s, akmc_stream stream) {
+    akmc_status st = sl_check(b, voxel, sector_cells, window_s);
+    if (st != AKMC_OK) return st;
+    if (n_supersteps == 0) return AKMC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->dirty) {
+        st = rebuild(b, s);
+        if (st != AKMC_OK) return st;
+    }
+    const BatchArgs a = b->args();
+    const int ns = b->desc[voxel].L / sector_cells, n_sec = ns * ns * ns;
+    int32_t* words = (int32_t*)(b->base + b->lo.sl_done);
+    AKMC_CUDA(cudaMemsetAsync(words, 0, sizeof(int32_t) * (4 + (size_t)n_sec), s));
+    int grid = 0;
+    cudaError_t e = launch_sublattice_async(a, voxel, (uint32_t)superstep0, n_supersteps, sector_cells, n_sec,
+                                            window_s, words + 4, words, b->n_sm, &grid, s);
+    if (e != cudaSuccess) return fail(AKMC_ECUDA, "asynchronous sublattice kernel: %s", cudaGetErrorString(e));
+    e = launch_rebuild(a, 8, (const int32_t*)(b->base + b->lo.ident) + voxel, 1, s);
+    if (e != cudaSuccess) return fail(AKMC_ECUDA, "rebuild kernel: %s", cudaGetErrorString(e));
+    return AKMC_OK;
+}
+
+akmc_status akmc_step_sublattice(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
+                                 int32_t sector_cells, double window_s, akmc_stream stream) {
+    {
+        akmc_status st0 = sl_check(b, voxel, sector_cells, window_s);
+        if (st0 != AKMC_OK) return st0;
+    }
+    const int L = b->desc[voxel].L, Sc = sector_cells;
     if (n_supersteps == 0) return AKMC_OK;
     cudaStream_t s = (cudaStream_t)stream;
     if (b->dirty) {

@@ -33,6 +33,13 @@ int step_occupancy(int warps, int max_nv, int max_P, int win);
 cudaError_t sl_prepare(const BatchArgs& a);
 cudaError_t launch_sublattice(const BatchArgs& a, int vid, uint32_t k, int sector_cells, int n_sectors,
                               double window, cudaStream_t st);
+// Asynchronous form: n supersteps from k0 in one cooperative launch of
+// min(n_sectors, resident CTAs) CTAs with per-sector readiness counters
+// done[n_sectors] (zeroed by the caller) and an abort word; grid_out gets the
+// grid size.
+cudaError_t launch_sublattice_async(const BatchArgs& a, int vid, uint32_t k0, uint32_t n, int sector_cells,
+                                    int n_sectors, double window, int32_t* done, int32_t* abort_flag, int n_sm,
+                                    int* grid_out, cudaStream_t st);
 
 const Tables& host_tables();   // stencil tables built on the host
 void set_last_error(const char* msg);   // text returned by akmc_last_error() on this thread

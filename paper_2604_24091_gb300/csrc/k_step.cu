@@ -26,6 +26,7 @@
 // memory while it is resident.  Every result is independent of the launch
 // shape: integer sums are order-free, and the FP64 mode rates hop k in one
 // warp with a fixed lane mapping and shuffle tree.
+#include <algorithm>
 #include <mutex>
 
 #include "akmc_device.cuh"
@@ -93,7 +94,7 @@ struct __align__(16) StepShared {
     double nx1, nx2;                  // uniforms of the event after the next one
     // sublattice superstep (see sl_kernel): counter words of the uniforms,
     // octant bounds (cells) and the octant's clock and window
-    int32_t sl_on, sl_k, sl_sid, sl_n;
+    int32_t sl_on, sl_k, sl_sid, sl_n, sl_nvtot, sl_etab;
     int32_t sl_x0, sl_y0, sl_z0, sl_h;
     double sl_t, sl_T;
 };
@@ -394,9 +395,9 @@ __device__ __forceinline__ void phase_gather(StepShared& S, const Dyn& D, int q,
         const int o = S.off[u];
         const int s = site_index(wrap_coord(X + off_dx(o), M2), wrap_coord(Y + off_dy(o), M2),
                                  wrap_coord(Z + off_dz(o), M2), L);
-        S.ssp[u] = S.v.species[s];
+        S.ssp[u] = S.sl_on ? __ldcg(S.v.species + s) : S.v.species[s];
         if (eam) {
-            int r = S.v.rho[s];
+            int r = S.sl_on ? __ldcg(S.v.rho + s) : S.v.rho[s];
             if (moved) {
                 const int ds = S.dsh[u][S.dir];
                 r += S.fq[S.A][ds >> 3] - S.fq[S.A][ds & 7];
@@ -430,8 +431,8 @@ __device__ __forceinline__ void phase_prefetch(StepShared& S, const Dyn& D, int 
         const int o = S.roff[i];
         const int s = site_index(wrap_coord(X + off_dx(o), M2), wrap_coord(Y + off_dy(o), M2),
                                  wrap_coord(Z + off_dz(o), M2), L);
-        S.rsp[i] = S.v.species[s];
-        if (MODE != 0) S.rrho[i] = S.v.rho[s];
+        S.rsp[i] = S.sl_on ? __ldcg(S.v.species + s) : S.v.species[s];
+        if (MODE != 0) S.rrho[i] = S.sl_on ? __ldcg(S.v.rho + s) : S.v.rho[s];
     }
 }
 
@@ -1402,28 +1403,17 @@ __device__ void run_events_sl(StepShared& S, const Dyn& D) {
     __syncthreads();
 }
 
-// One superstep k of voxel `vid`, one CTA per sector (grid (L/Sc)^3).
+// One sector's share of superstep k: the vacancies inside its active octant
+// (slot order), their rates from the current lattice, then the events.
+// Returns the events made (uniform).  Lattice, densities and vacancy records
+// are read with L2-only loads (other CTAs write them during the asynchronous
+// kernel).  S.v must hold the voxel, S.sl_nvtot its vacancy count.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint32_t k, int Sc, double T) {
-    extern __shared__ __align__(16) unsigned char dyn_raw[];
-    __shared__ StepShared S;
+__device__ uint64_t sl_sector(StepShared& S, const Dyn& D, const Tables* tab, uint32_t k, int sid, int Sc,
+                              double T) {
     constexpr int NT = NW * 32;
-    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
-    const int tid = threadIdx.x, sid = blockIdx.x;
-    VoxelDev* gv = &a.vox[vid];
-    load_model<NW>(S, a.model);
+    const int tid = threadIdx.x;
     if (tid == 0) {
-        S.v = *gv;
-        if (sid == 0 && S.v.status == kOK) {   // the voxel clock: T/8 per superstep, compensated
-            const double dt = T * 0.125, hi = S.v.t_hi + dt;
-            double lo = S.v.t_lo;
-            if (fabs(S.v.t_hi) >= fabs(dt))
-                lo += (S.v.t_hi - hi) + dt;
-            else
-                lo += (dt - hi) + S.v.t_hi;
-            gv->t_hi = hi;
-            gv->t_lo = lo;
-        }
         const int ns = S.v.L / Sc, h = Sc / 2, oct = (int)(k & 7u);
         S.sl_h = h;
         S.sl_x0 = (sid % ns) * Sc + (oct & 1) * h;
@@ -1431,16 +1421,15 @@ __global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint3
         S.sl_z0 = (sid / (ns * ns)) * Sc + ((oct >> 2) & 1) * h;
     }
     __syncthreads();
-    if (S.v.status != kOK) return;   // uniform
-    // the active vacancies, in slot order
+    const int L = S.v.L;
     if (tid < 32) {
-        const int L = S.v.L, nv = S.v.nv;
+        const int nv = S.sl_nvtot;
         int n = 0;
         for (int b = 0; b < nv; b += 32) {
             const int q = b + tid;
             bool in = false;
             if (q < nv) {
-                const int s = S.v.vac_pos[q], c = s >> 1, bit = s & 1;
+                const int s = __ldcg(S.v.vac_pos + q), c = s >> 1, bit = s & 1;
                 in = sl_inside(S, 2 * (c % L) + bit, 2 * ((c / L) % L) + bit, 2 * (c / (L * L)) + bit);
             }
             const unsigned m = __ballot_sync(0xffffffffu, in);
@@ -1451,30 +1440,30 @@ __global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint3
     }
     __syncthreads();
     const int n_act = S.sl_n;
-    if (n_act == 0) return;   // uniform
-    load_tables<NW>(S, a.tab, S.v.model, 0);
+    if (n_act == 0) return 0;   // uniform
+    load_tables<NW>(S, tab, S.v.model, 0);
+    if (!S.sl_etab) {   // uniform
+        for (int i = tid; i < kEtab; i += NT) D.etab[i] = S.v.etab[i];
+    }
     int P = 1;
     while (P < n_act) P <<= 1;
-    const int L = S.v.L;
     for (int j = tid; j < n_act; j += NT) {
-        const int q = D.gslot[j], s = S.v.vac_pos[q], c = s >> 1, bit = s & 1;
+        const int q = D.gslot[j], s = __ldcg(S.v.vac_pos + q), c = s >> 1, bit = s & 1;
         D.pos[j] = s;
         D.X[j] = 2 * (c % L) + bit;
         D.Y[j] = 2 * ((c / L) % L) + bit;
         D.Z[j] = 2 * (c / (L * L)) + bit;
-        D.disp[3 * j + 0] = S.v.vac_disp[3 * q + 0];
-        D.disp[3 * j + 1] = S.v.vac_disp[3 * q + 1];
-        D.disp[3 * j + 2] = S.v.vac_disp[3 * q + 2];
+        D.disp[3 * j + 0] = __ldcg(S.v.vac_disp + 3 * q + 0);
+        D.disp[3 * j + 1] = __ldcg(S.v.vac_disp + 3 * q + 1);
+        D.disp[3 * j + 2] = __ldcg(S.v.vac_disp + 3 * q + 2);
         D.on[j] = 1;
     }
     for (int i = tid; i < 2 * P; i += NT) D.tree[i] = 0.0;
-    for (int i = tid; i < kEtab; i += NT) D.etab[i] = S.v.etab[i];
     __syncthreads();
     if (tid == 0) {
+        S.sl_etab = 1;
         S.v.nv = n_act;
         S.v.P = P;
-        S.v.log_cap = 0;
-        S.sl_on = 1;
         S.sl_k = (int32_t)k;
         S.sl_sid = sid;
         S.sl_t = 0.0;
@@ -1509,10 +1498,136 @@ __global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint3
         S.v.vac_disp[3 * q + 1] = D.disp[3 * j + 1];
         S.v.vac_disp[3 * q + 2] = D.disp[3 * j + 2];
     }
-    if (tid == 0) {
-        if (S.n) atomicAdd((unsigned long long*)&gv->n_events, (unsigned long long)S.n);
+    return S.n;
+}
+
+// Voxel state for the sublattice kernels: the voxel record, no event log,
+// L2-only lattice loads.  Returns false (uniform) if the voxel is not OK.
+template <int NW>
+__device__ bool sl_begin(StepShared& S, const BatchArgs& a, int vid) {
+    load_model<NW>(S, a.model);
+    if (threadIdx.x == 0) {
+        S.v = a.vox[vid];
+        S.sl_nvtot = S.v.nv;
+        S.v.log_cap = 0;
+        S.sl_on = 1;
+        S.sl_etab = 0;
+    }
+    __syncthreads();
+    return S.v.status == kOK;
+}
+
+__device__ __forceinline__ void sl_clock(VoxelDev* gv, double t_hi, double t_lo, double dt, uint32_t n) {
+    for (uint32_t i = 0; i < n; ++i) {
+        const double hi = t_hi + dt;
+        if (fabs(t_hi) >= fabs(dt))
+            t_lo += (t_hi - hi) + dt;
+        else
+            t_lo += (dt - hi) + t_hi;
+        t_hi = hi;
+    }
+    gv->t_hi = t_hi;
+    gv->t_lo = t_lo;
+}
+
+// Synchronous form: superstep k of voxel `vid`, one CTA per sector (grid
+// (L/Sc)^3); the kernel boundary is the global barrier between supersteps.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint32_t k, int Sc, double T) {
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    __shared__ StepShared S;
+    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
+    VoxelDev* gv = &a.vox[vid];
+    if (!sl_begin<NW>(S, a, vid)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sl_clock(gv, S.v.t_hi, S.v.t_lo, T * 0.125, 1);
+    const uint64_t made = sl_sector<NW>(S, D, a.tab, k, blockIdx.x, Sc, T);
+    if (threadIdx.x == 0) {
+        if (made) atomicAdd((unsigned long long*)&gv->n_events, (unsigned long long)made);
         if (S.v.status != kOK) atomicCAS(&gv->status, kOK, S.v.status);
     }
+}
+
+// Asynchronous form (the readiness scheme of the sublattice method): one
+// cooperative launch runs all n supersteps; CTA c owns sectors c, c + G, ...
+// and takes its tasks (superstep i, sector) in superstep order.  done[s] = i
+// records that sector s has finished supersteps < i; sector s starts
+// superstep i once its 26 neighbours have done[.] >= i -- the only sectors
+// whose superstep i - 1 can touch what superstep i of s reads or writes.
+// Neighbouring sectors thus run the same superstep concurrently and never
+// different ones, so the result equals the synchronous schedule; distant
+// sectors drift apart freely.  All CTAs are resident (cooperative launch),
+// and the smallest unfinished task always has its inputs ready, so the waits
+// end; each wait is still bounded (a few seconds), after which the voxel gets
+// kETIMEOUT and every CTA leaves at its next wait.
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Warp 0: wait until the 26 neighbours of sector sid have done >= need.
+// Returns false (to lane 0..31) on abort or timeout.
+__device__ bool sl_wait(const int32_t* done, int32_t* abort_flag, int sid, int ns, int need, VoxelDev* gv) {
+    const int lane = threadIdx.x & 31;
+    int nb = sid;
+    if (lane < 27 && lane != 13) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        const int sx = sid % ns, sy = (sid / ns) % ns, sz = sid / (ns * ns);
+        nb = (((sz + dz + ns) % ns) * ns + (sy + dy + ns) % ns) * ns + (sx + dx + ns) % ns;
+    }
+    for (int it = 0; it < (1 << 22); ++it) {
+        const bool ok = ld_acquire(done + nb) >= need || nb == sid;
+        const int ab = lane == 0 ? ld_acquire(abort_flag) : 0;
+        if (__shfl_sync(0xffffffffu, ab, 0)) return false;
+        if (__all_sync(0xffffffffu, ok)) return true;
+        __nanosleep(200);
+    }
+    if (lane == 0) {
+        atomicExch(abort_flag, 1);
+        atomicCAS(&gv->status, kOK, kETIMEOUT);
+    }
+    return false;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) sl_async_kernel(BatchArgs a, int vid, uint32_t k0, uint32_t n, int Sc,
+                                                           double T, int32_t* done, int32_t* abort_flag) {
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    __shared__ StepShared S;
+    __shared__ int go;
+    const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
+    VoxelDev* gv = &a.vox[vid];
+    if (!sl_begin<NW>(S, a, vid)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sl_clock(gv, S.v.t_hi, S.v.t_lo, T * 0.125, n);
+    const int ns = S.v.L / Sc, n_sec = ns * ns * ns;
+    uint64_t made = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        for (int sid = blockIdx.x; sid < n_sec; sid += gridDim.x) {
+            if (threadIdx.x < 32) {
+                const bool ok = sl_wait(done, abort_flag, sid, ns, (int)i, gv);
+                if (threadIdx.x == 0) go = ok;
+            }
+            __syncthreads();
+            if (!go) goto out;   // uniform
+            made += sl_sector<NW>(S, D, a.tab, k0 + i, sid, Sc, T);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (S.v.status != kOK) {
+                    atomicCAS(&gv->status, kOK, S.v.status);
+                    atomicExch(abort_flag, 1);
+                }
+                st_release(done + sid, (int)i + 1);
+            }
+            if (S.v.status != kOK) goto out;   // uniform
+        }
+    }
+out:
+    if (threadIdx.x == 0 && made) atomicAdd((unsigned long long*)&gv->n_events, (unsigned long long)made);
 }
 
 // Full rebuild of one voxel per CTA: every vacancy's rates, then the tree
@@ -1623,6 +1738,23 @@ cudaError_t launch_sublattice(const BatchArgs& a, int vid, uint32_t k, int secto
                               double window, cudaStream_t st) {
     sl_kernel<8><<<n_sectors, 256, step_dyn_smem(a.max_nv, a.max_P, 0), st>>>(a, vid, k, sector_cells, window);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sublattice_async(const BatchArgs& a, int vid, uint32_t k0, uint32_t n, int sector_cells,
+                                    int n_sectors, double window, int32_t* done, int32_t* abort_flag, int n_sm,
+                                    int* grid_out, cudaStream_t st) {
+    const size_t dyn = step_dyn_smem(a.max_nv, a.max_P, 0);
+    cudaError_t e = set_smem<8>((const void*)sl_async_kernel<8>, dyn);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sl_async_kernel<8>, 256, dyn);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = std::min(n_sectors, per_sm * n_sm);
+    *grid_out = grid;
+    void* args[] = {(void*)&a, (void*)&vid, (void*)&k0, (void*)&n, (void*)&sector_cells, (void*)&window,
+                    (void*)&done, (void*)&abort_flag};
+    return cudaLaunchCooperativeKernel((const void*)sl_async_kernel<8>, dim3(grid), dim3(256), args, dyn, st);
 }
 
 // The dynamic shared-memory attribute only ever grows (per device and kernel),

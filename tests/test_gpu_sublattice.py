@@ -142,3 +142,51 @@ def test_fp64_eam_larger_voxel_bit_exact(model):
     assert np.array_equal(g["vac_disp"], so["vac_disp"])
     np.testing.assert_array_equal(b.read_density(0).astype(np.int64), o.rho_all())
     b.close()
+
+
+@pytest.mark.parametrize("mdl,prec,L,Sc,nv", [(synth.PAIR_MODEL, synth.PREC_FP64, 16, 8, 12),
+                                               (synth.PAIR_MODEL, synth.PREC_FP64, 24, 8, 30),
+                                               (synth.EAM_MODEL, synth.PREC_FP64, 32, 8, 24)])
+def test_async_readiness_matches_oracle(model, mdl, prec, L, Sc, nv):
+    # one cooperative launch with per-sector readiness: the same result as the
+    # synchronous schedule, bit for bit
+    d = synth.VoxelDesc(L, nv, (0.06, 0.04, 0.04), 563.0, mdl, prec, seed=23 + L, uid=60 + nv)
+    o = oracle.Voxel(d, model)
+    T = _window(o, nv, 3.0)
+    b = Batch([d], model)
+    b.step_sublattice(0, 3, 40, Sc, T, asynchronous=True)
+    b.step_sublattice(0, 43, 9, Sc, T, asynchronous=True)
+    assert b.sync_status()[0] == 0
+    per_o = o.step_sublattice(3, 49, Sc, T)
+    g = b.read_state(0)
+    so = o.state()
+    assert g["n_events"] == so["n_events"] == per_o.sum() > 0
+    assert np.array_equal(g["species"], so["species"])
+    assert np.array_equal(g["vac_pos"], so["vac_pos"])
+    assert np.array_equal(g["vac_disp"], so["vac_disp"])
+    assert g["t_hi"] == so["t_hi"] and g["t_lo"] == so["t_lo"]
+    np.testing.assert_allclose(g["rates"], so["rates"], rtol=1e-12, atol=0)
+    if mdl == synth.EAM_MODEL:
+        np.testing.assert_array_equal(b.read_density(0).astype(np.int64), o.rho_all())
+    b.close()
+
+
+@pytest.mark.parametrize("Sc", [8, 16])
+def test_async_equals_sync_large_split(model, Sc):
+    # the large configuration in split precision: both forms on the GPU agree
+    # exactly (lattice, densities, vacancies, counters, clock)
+    d = synth.config_large()[0]
+    bs, ba = Batch([d], model), Batch([d], model)
+    r = float(bs.read_state(0)["rates"].sum())
+    T = 4.0 / (r / d.n_vac)
+    bs.step_sublattice(0, 0, 64, Sc, T)
+    ba.step_sublattice(0, 0, 64, Sc, T, asynchronous=True)
+    assert bs.sync_status()[0] == 0 and ba.sync_status()[0] == 0
+    gs, ga = bs.read_state(0), ba.read_state(0)
+    assert gs["n_events"] == ga["n_events"] > 64 * 64 / 8
+    for k in ("species", "vac_pos", "vac_disp"):
+        assert np.array_equal(gs[k], ga[k]), k
+    assert gs["t_hi"] == ga["t_hi"] and gs["t_lo"] == ga["t_lo"]
+    assert np.array_equal(bs.read_density(0), ba.read_density(0))
+    bs.close()
+    ba.close()
