@@ -341,6 +341,34 @@ def logit_select_leg(torch, dev, peak, peak_kind):
             "workload": "256 systems x 524288 logits (float32) + mask (uint8), 671 MB", "ms": 1e3 * min(ts)}
 
 
+def sublattice_leg(model, torch, Batch, sector_cells=16, n_st=800, windows=(1.0, 4.0)):
+    """The large configuration (128^3 cells, 64 vacancies, EAM split) under
+    sublattice supersteps, synchronous (one launch per superstep) and
+    asynchronous (one launch, per-sector readiness): sectors of 16 cells, windows
+    sized for f events per active vacancy.  The yield is the events made over
+    the events the global rate makes in the same voxel time (R_tot T/8 per
+    superstep): what the octant boundaries cost."""
+    cfg = synth.config_large()
+    out = {"config": "1 voxel of 128^3 cells, 64 vacancies, EAM split, sectors of %d cells, %d supersteps"
+                     % (sector_cells, n_st)}
+    for f in windows:
+        for form in ("sync", "async"):
+            lb = Batch(cfg, model)
+            r_tot = float(lb.read_state(0)["rates"].sum())
+            T = f / (r_tot / cfg[0].n_vac)
+            asy = form == "async"
+            lb.step_sublattice(0, 0, 16, sector_cells, T, asynchronous=asy)
+            n0 = lb.read_state(0)["n_events"]
+            t = _time_region(lambda: lb.step_sublattice(0, 16, n_st, sector_cells, T, asynchronous=asy), torch)
+            st, _ = lb.sync_status()
+            made = lb.read_state(0)["n_events"] - n0
+            out["%s_f%g" % (form, f)] = {"value": made / t, "unit": UNIT, "status": st, "window_s": T,
+                                         "events_per_superstep": made / n_st, "supersteps_per_s": n_st / t,
+                                         "yield": made / (n_st * r_tot * T / 8)}
+            lb.close()
+    return out
+
+
 def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
     out = {}
     # end to end through the public API with pinned host buffers: load the
@@ -394,6 +422,7 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
                                "1e4 events per vacancy" if key == "uneven" else
                                "1 voxel of 128^3 cells, 64 vacancies, EAM split, 2e4 events")}
         ub.close()
+    out["large_sublattice"] = sublattice_leg(model, torch, Batch)
     # the oracle on the host cores, bounded sample of the same workload
     procs = os.cpu_count() or 1
     per = 3 * args.ref_events
