@@ -271,7 +271,8 @@ struct Layout {
     std::vector<int4> item_list;       // density tiles (voxels with L > kStripMaxL)
     std::vector<int4> strip_list;      // density strips (voxels with L <= kStripMaxL)
     size_t strips = 0, reset_strips = 0;
-    int strip_ty = 16, strip_lmax = 0;
+    int strip_lmax = 0;
+    size_t strip_dyn = 0;              // dynamic shared memory of the strip kernel (batch maximum)
     int max_nv = 1, max_P = 1, win = 0;
     size_t max_N = 0;
     bool has_eam = false;
@@ -314,20 +315,18 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
                 for (int y = 0; y < L; y += kTY)
                     for (int x = 0; x < L; x += kTX) Lo.item_list.push_back(make_int4(v, x, y, z));
         }
-        // Strips: ty rows per strip (bounded by shared memory and by one 16-byte
-        // chunk of the haloed strip per thread); the z extent tz is the largest
-        // of {L, 64, 32, 16, 8} that still gives >= 1024 strips (several waves).
+        // Strips: density_strip_rows(L) rows per strip (bounded by shared memory
+        // and by the 16-byte chunks a thread holds); the z extent tz is the
+        // largest of {L, 64, 32, 16, 8} that still gives >= 1024 strips (several waves).
         if (Lo.strip_lmax > 0) {
-            const int lm = Lo.strip_lmax;
-            Lo.strip_ty = lm <= 64 ? 16 : (lm <= 128 ? 8 : 4);
             const int cand[5] = {1 << 30, 64, 32, 16, 8};
             int tz_cap = 8;
             for (int ci = 0; ci < 5; ++ci) {
                 long long cnt = 0;
                 for (int32_t v = 0; v < n; ++v) {
                     if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL) continue;
-                    const int L = d[v].L, tz = std::min(cand[ci], L);
-                    cnt += (long long)((L + Lo.strip_ty - 1) / Lo.strip_ty) * ((L + tz - 1) / tz);
+                    const int L = d[v].L, tz = std::min(cand[ci], L), ty = density_strip_rows(L);
+                    cnt += (long long)((L + ty - 1) / ty) * ((L + tz - 1) / tz);
                 }
                 if (cnt >= 1024) {
                     tz_cap = cand[ci];
@@ -336,10 +335,11 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
             }
             for (int32_t v = 0; v < n; ++v) {
                 if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL) continue;
-                const int L = d[v].L, tz = std::min(tz_cap, L);
+                const int L = d[v].L, tz = std::min(tz_cap, L), ty = density_strip_rows(L);
+                Lo.strip_dyn = std::max(Lo.strip_dyn, density_strip_smem(L));
                 for (int z = 0; z < L; z += tz)
-                    for (int y = 0; y < L; y += Lo.strip_ty)
-                        Lo.strip_list.push_back(make_int4(v, y, z, std::min(tz, L - z)));
+                    for (int y = 0; y < L; y += ty)
+                        Lo.strip_list.push_back(make_int4(v, y, z, std::min(tz, L - z) | (ty << 17)));
             }
         }
         Lo.items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
@@ -452,7 +452,7 @@ akmc_status rebuild(akmc_batch* b, cudaStream_t st) {
     if (b->lo.has_eam && (!b->lo.item_list.empty() || !b->lo.strip_list.empty())) {
         cudaError_t e = launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + b->lo.items),
                                        (int)b->lo.item_list.size(), (const int4*)(b->base + b->lo.strips),
-                                       (int)b->lo.strip_list.size(), b->lo.strip_ty, b->lo.strip_lmax, st);
+                                       (int)b->lo.strip_list.size(), b->lo.strip_dyn, st);
         if (e != cudaSuccess) return fail(AKMC_ECUDA, "density kernel: %s", cudaGetErrorString(e));
     }
     cudaError_t e = launch_rebuild(a, 8, nullptr, 0, st);
@@ -814,8 +814,7 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
                                   cudaMemcpyHostToDevice, s));
     if (!items.empty() || !strips.empty())
         AKMC_CUDA(launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + lo.reset_items), (int)items.size(),
-                                 (const int4*)(b->base + lo.reset_strips), (int)strips.size(), lo.strip_ty,
-                                 lo.strip_lmax, s));
+                                 (const int4*)(b->base + lo.reset_strips), (int)strips.size(), lo.strip_dyn, s));
     AKMC_CUDA(launch_rebuild(a, 8, list, n, s));
     // pageable sources above are staged by the copies; the tile list must outlive its copy
     AKMC_CUDA(cudaStreamSynchronize(s));

@@ -14,12 +14,15 @@ cudaError_t launch_batch_read(const VoxelDev* vox, double* io, int n, cudaStream
 
 // Density tiles: cells [x0,x0+kTX) x [y0,y0+kTY) x [z0,z0+kTZ) of one voxel.
 constexpr int kTX = 32, kTY = 16, kTZ = 16, kHalo = 2;
-// Strips (voxels with L <= kStripMaxL): item (voxel, y0, z0, tz | vec << 16)
-// covers rows [y0, y0+ty) of planes [z0, z0+tz); vec = 16-byte aligned rows.
+// Strips (voxels with L <= kStripMaxL): item (voxel, y0, z0, tz | vec << 16 | ty << 17)
+// covers rows [y0, y0+ty) of planes [z0, z0+tz); vec = 16-byte aligned rows;
+// ty = density_strip_rows(L); a strip of a voxel of edge L needs
+// density_strip_smem(L) bytes of dynamic shared memory (strip_dyn: the batch maximum).
 constexpr int kStripMaxL = 256;
+int density_strip_rows(int L);
+size_t density_strip_smem(int L);
 cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
-                           int n_tiles, const int4* strips, int n_strips, int strip_ty, int strip_lmax,
-                           cudaStream_t st);
+                           int n_tiles, const int4* strips, int n_strips, size_t strip_dyn, cudaStream_t st);
 
 size_t step_dyn_smem(int max_nv, int max_P, int win);
 cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, const int32_t* list,

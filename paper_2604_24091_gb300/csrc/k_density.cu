@@ -109,19 +109,32 @@ __global__ void __launch_bounds__(kDensThreads) density_tile_kernel(const VoxelD
 
 // ---- strip kernel: full x-rows, streamed along z -----------------------------
 // One CTA owns the rows y in [y0, y0+ty) of the planes z in [z0, z0+tz) of one
-// voxel.  It walks the source planes z0-2 .. z0+tz+1 once, in order: each
-// plane's haloed strip of species rows (ty+4 rows of 2L sites, one 16-byte
-// vector load per thread, prefetched one plane ahead) is scanned for non-Fe
-// sites, which are appended to a list (warp scan, one shared atomic per
-// warp); then 8 lanes per listed site add its 58 corrections f_s - f_Fe to a
-// buffer of 8 density planes in shared memory (each lane 7 or 8 offsets, the
-// offsets' buffer deltas held in registers).  The buffer holds planes
-// [qb, qb+8); after the 4 source planes qb+2 .. qb+5 the planes qb .. qb+3 are
-// complete: they are written to memory with 16-byte stores (planes outside
-// the CTA's range are dropped), planes qb+4 .. qb+7 move down and the top
-// half restarts as pure Fe.  Rows are padded by 4 sites on each side, so an x
-// offset needs no wrap: the pads are folded into the row ends when a plane is
-// written.
+// voxel.  It walks the source planes z0-2 .. z0+tz+1 once, in blocks of 4.
+// Per block:
+//  a. append: the block's haloed strips (ty+4 rows of 2L sites per plane,
+//     16-byte chunks, loaded one block ahead into registers) are scanned for
+//     non-Fe bytes with a few word
+//     operations per 4 sites; each non-Fe site becomes one list entry
+//     (species, buffer position, halo row), in one list per sublattice
+//     (b = X & 1): entries of the strip's own rows at the front, of the 2 + 2
+//     halo rows at the back;
+//  b. scatter (all warps): warps 0, 2, 4, 6 take the b = 0 list and warps
+//     1, 3, 5, 7 the b = 1 list, 8 lanes per entry; a lane holds the
+//     shared-memory byte deltas of its 8 stencil offsets for its warp's b
+//     (registers) and fetches the entry species' weights f_s - f_Fe with two
+//     16-byte loads, then adds them to a buffer of 8 density planes with
+//     shared-memory reductions (integer, hence order-independent).  Every
+//     plane has 2 guard rows on each side, so the strip's own rows need no
+//     check; halo-row entries predicate each term on its target row;
+//  c. pads: the row pads (4 sites on each side, so an x offset needs no wrap)
+//     of buffer planes 0..3 are folded into the row ends, planes 4..7's pads
+//     move down;
+//  d. shift: planes 0..3 are complete and written with 16-byte stores (planes
+//     outside the CTA's z range are dropped); planes 4..7 move down and
+//     restart as pure Fe.  Four barriers per block.
+// A block whose lists would overflow (a locally dense lattice, > 1024 entries
+// of one sublattice) is scattered directly from memory instead, one site per
+// thread (slow, exact).
 //
 // Site coordinates: within a row (fixed y, z) the site index 2x+b equals the
 // half-unit coordinate X, so a neighbour at half-unit offset dx sits at
@@ -129,300 +142,307 @@ __global__ void __launch_bounds__(kDensThreads) density_tile_kernel(const VoxelD
 //
 // Per output site the work is one species byte read, one density write and,
 // for the ~2% non-Fe sites (x the halo factor (ty+4)/ty * (tz+4)/tz), 58
-// shared-memory atomics.
+// shared-memory reductions.
 
 constexpr int kStripThreads = 256;
-constexpr int kStripWarps = kStripThreads / 32;
-constexpr int kPlanes = 8;          // density planes held
-constexpr int kShift = 4;           // planes completed per block of source planes
+constexpr int kBlk = 4;             // source planes per block
+constexpr int kPlanes = kBlk + 4;   // density planes held
 constexpr int kRowPad = 4;          // padding sites on each side of a buffer row
-constexpr int kLanesPerSite = 8;    // scatter lanes per listed site
+constexpr int kGuard = 2;           // guard rows on each side of a buffer plane
+constexpr int kChunks = 3;          // 16-byte chunks per thread and block (host-guaranteed)
+constexpr int kStripCap = 1024;     // entries per sublattice list and block
+constexpr int kOffs = 8;            // stencil offsets per scatter lane: k = sub + 8j
 
 __host__ __device__ inline int strip_rw(int L) { return 2 * L + 2 * kRowPad; }
-__host__ __device__ inline int strip_slot(int TY, int L) { return TY * strip_rw(L) + 4; }
+__host__ __device__ inline int strip_slot(int TY, int L) { return (TY + 2 * kGuard) * strip_rw(L) + 4; }
+// buffer planes and two lists
+__host__ __device__ inline size_t strip_smem(int TY, int L) {
+    return sizeof(int32_t) * ((size_t)kPlanes * strip_slot(TY, L) + 2 * (size_t)kStripCap);
+}
+// rows per strip: 16 for L <= 64, 8 for L <= 128, 2 beyond (shared memory and kChunks)
+__host__ __device__ inline int strip_rows(int L) { return L <= 64 ? 16 : (L <= 128 ? 8 : 2); }
 
 // floor((b + d) / 2) for b in {0,1}, d in [-4, 4]
 __device__ __forceinline__ int half_floor(int v) { return (v + 8) / 2 - 4; }
 
-// Entries of rows hr in [4, ty) reach only rows inside the strip and go to the
-// front of the list (count[0]); the others go to the back (count[1], list
-// index cap - 1 - i) and are scattered with a row check.
-__device__ __forceinline__ bool strip_inner(int hr, int ty) { return hr >= 4 && hr < ty; }
-
-template <bool VEC>
-__device__ __forceinline__ void strip_append(const uint8_t* sp, int L, int zp, int y0, int ty, uint4 pre,
-                                             int my_hr, int my_cx, uint32_t* list, int cap, int* count) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int M2 = 2 * L;
-    if (VEC) {
-        // the chunk this thread loaded: 16 sites X = 16 cx .. 16 cx + 15 of halo row hr
-        uint32_t M = 0;
-        if (my_hr >= 0) {
-            const uint32_t w[4] = {pre.x, pre.y, pre.z, pre.w};
+// Bit j of the result: byte j of the 16-byte chunk is non-zero.
+__device__ __forceinline__ uint32_t nonzero_bytes(uint4 v) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t M = 0;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                uint32_t t = w[i] | (w[i] >> 4);
-                t |= t >> 2;
-                t |= t >> 1;
-                t &= 0x01010101u;                       // bit 0 of each byte: byte != 0
-                M |= ((t | (t >> 7) | (t >> 14) | (t >> 21)) & 0xFu) << (4 * i);
-            }
-        }
-        if (M) {
-            const int c = __popc(M);
-            const bool in = strip_inner(my_hr, ty);
-            const int at0 = atomicAdd(&count[in ? 0 : 1], c);
-            int i = 0;
-            while (M) {
-                const int j = __ffs(M) - 1;
-                M &= M - 1;
-                const uint32_t wj = j < 8 ? (j < 4 ? pre.x : pre.y) : (j < 12 ? pre.z : pre.w);
-                const uint32_t s = (wj >> (8 * (j & 3))) & 0xFFu;
-                const uint32_t en = (s > 7 ? 7u : s) | ((uint32_t)(16 * my_cx + j) << 3) | ((uint32_t)my_hr << 13);
-                list[in ? at0 + i : cap - 1 - (at0 + i)] = en;
-                ++i;
-            }
-        }
-        (void)lane;
-    } else {
-        // byte path (rows not 16-byte aligned): one byte per thread and pass
-        const int n = (ty + 4) * M2;
-        for (int c0 = 0; c0 < n; c0 += kStripThreads) {
-            const int c = c0 + tid;
-            uint32_t s = 0;
-            int hr = 0, X = 0;
-            if (c < n) {
-                hr = c / M2;
-                X = c - hr * M2;
-                int y = y0 - 2 + hr;
-                y = y < 0 ? y + L : (y >= L ? y - L : y);
-                s = sp[((size_t)zp * L + y) * M2 + X];
-            }
-            const bool hit = s != 0, in = strip_inner(hr, ty);
-            const unsigned mi = __ballot_sync(0xffffffffu, hit && in), me = __ballot_sync(0xffffffffu, hit && !in);
-            int bi = 0, be = 0;
-            if (lane == 0 && mi) bi = atomicAdd(&count[0], __popc(mi));
-            if (lane == 0 && me) be = atomicAdd(&count[1], __popc(me));
-            bi = __shfl_sync(0xffffffffu, bi, 0);
-            be = __shfl_sync(0xffffffffu, be, 0);
-            const uint32_t en = (s > 7 ? 7u : s) | ((uint32_t)X << 3) | ((uint32_t)hr << 13);
-            if (hit && in) list[bi + __popc(mi & ((1u << lane) - 1u))] = en;
-            if (hit && !in) list[cap - 1 - (be + __popc(me & ((1u << lane) - 1u)))] = en;
-        }
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t t = (((w[i] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[i]) & 0x80808080u;   // bit 7 per byte
+        M |= (((t >> 7) * 0x10204080u) >> 28) << (4 * i);                                 // bits 0, 8, 16, 24 -> 0..3
     }
+    return M;
 }
 
-// Planes buf[0..3] are complete: write those inside the CTA's range (rel. plane
-// q in [2, tz+2), i.e. z = z0 + q - 2), move buf[4..7] down, reset buf[4..7].
-// Every element is read, moved and reset by the same thread.
-template <bool VEC>
-__device__ void strip_shift(const VoxelDev& V, int32_t* buf, int SLOT, int RW, int ty, int y0, int z0, int qb,
-                            int tz, int32_t rho0) {
-    const int L = V.L, M2 = 2 * L;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (VEC) {
-        const int C = RW / 4;                     // int4 per padded row (RW = 2L + 8, L even)
-        const int c_first = kRowPad / 4, c_last = (kRowPad + M2) / 4 - 1;
-        const int4 pure = make_int4(rho0, rho0, rho0, rho0), zero = make_int4(0, 0, 0, 0);
-        for (int r = warp; r < ty; r += kStripWarps) {
-            for (int c = lane; c < C; c += 32) {
-                if (c < c_first || c > c_last) continue;
-#pragma unroll
-                for (int i = 0; i < kShift; ++i) {
-                    const int32_t* row = buf + i * SLOT + r * RW;
-                    const int q = qb + i;
-                    if (q < 2 || q >= tz + 2) continue;
-                    int4 v = *(const int4*)(row + 4 * c);
-                    if (c == c_first) {            // sites 0..2 collect the right pads (X = 2L .. 2L+2)
-                        v.x += row[kRowPad + M2];
-                        v.y += row[kRowPad + M2 + 1];
-                        v.z += row[kRowPad + M2 + 2];
-                    }
-                    if (c == c_last) {             // sites 2L-3..2L-1 collect the left pads (X = -3 .. -1)
-                        v.y += row[kRowPad - 3];
-                        v.z += row[kRowPad - 2];
-                        v.w += row[kRowPad - 1];
-                    }
-                    *(int4*)(V.rho + ((size_t)(z0 + q - 2) * L + y0 + r) * M2 + 4 * (c - c_first)) = v;
-                }
-            }
-            __syncwarp();   // every read of this row (pads included) precedes the moves below
-            for (int c = lane; c < C; c += 32) {
-                const bool site = c >= c_first && c <= c_last;
-#pragma unroll
-                for (int i = 0; i < kShift; ++i) {
-                    int32_t* row = buf + i * SLOT + r * RW;
-                    int32_t* up = buf + (i + kShift) * SLOT + r * RW;
-                    *(int4*)(row + 4 * c) = *(const int4*)(up + 4 * c);
-                    *(int4*)(up + 4 * c) = site ? pure : zero;
-                }
-            }
-        }
-    } else {
-        for (int r = warp; r < ty; r += kStripWarps) {
-            for (int i = 0; i < kShift; ++i) {
-                int32_t* row = buf + i * SLOT + r * RW + kRowPad;
-                const int q = qb + i;
-                if (q >= 2 && q < tz + 2) {
-                    int32_t* out = V.rho + ((size_t)(z0 + q - 2) * L + y0 + r) * M2;
-                    for (int c = lane; c < M2; c += 32) {
-                        int v = row[c];
-                        if (c < 3) v += row[M2 + c];
-                        if (c >= M2 - 3) v += row[c - M2];
-                        out[c] = v;
-                    }
-                }
-            }
-            __syncwarp();
-            for (int i = 0; i < kShift; ++i) {
-                int32_t* row = buf + i * SLOT + r * RW;
-                int32_t* up = buf + (i + kShift) * SLOT + r * RW;
-                for (int c = lane; c < RW; c += 32) {
-                    row[c] = up[c];
-                    up[c] = (c >= kRowPad && c < kRowPad + M2) ? rho0 : 0;
-                }
-            }
-        }
-    }
+// Entry: species (3 bits, codes above 7 clamped) | buffer position u << 3 | halo row << 23,
+// u = (plane in block + 2) * SLOT + hr * RW + X + kRowPad (halo row hr = buffer row).
+__device__ __forceinline__ uint32_t strip_entry(uint32_t s, int u, int hr) {
+    return (s > 7 ? 7u : s) | ((uint32_t)u << 3) | ((uint32_t)hr << 23);
+}
+
+// Halo rows hr in [2, ty+2) are the strip's own rows: every target lies in the buffer.
+__device__ __forceinline__ bool strip_own(int hr, int ty) { return hr >= 2 && hr < ty + 2; }
+
+__device__ __forceinline__ void strip_push(uint32_t* lists, uint32_t en, int b, bool own, int at) {
+    if (at < kStripCap) lists[b * kStripCap + (own ? at : kStripCap - 1 - at)] = en;
+}
+
+// shared-memory reduction at byte address a; the predicated form adds iff row < ty
+__device__ __forceinline__ void red_add(uint32_t a, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_if(uint32_t a, int v, uint32_t row, uint32_t ty) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %2, %3;\n\t@p red.shared.add.s32 [%0], %1;\n\t}" ::"r"(a), "r"(v),
+                 "r"(row), "r"(ty)
+                 : "memory");
+}
+
+// Weight f_s - f_Fe of stencil offset k for species s (table [s][k & 7][k >> 3]).
+__device__ __forceinline__ int strip_w(const int4 (*wt)[8][2], int s, int k) {
+    return ((const int32_t*)wt)[s * 64 + (k & 7) * 8 + (k >> 3)];
 }
 
 template <bool VEC>
-__device__ void strip_body(const VoxelDev& V, const int4 it, int TY, int32_t* buf, uint32_t* lists, int list_cap,
-                           const int32_t (*cq)[8], const int32_t* sph, int* counts, int32_t rho0) {
+__device__ void strip_body(const VoxelDev& V, const int4 it, int32_t* buf, uint32_t* lists,
+                           const int4 (*wt)[8][2], const int32_t* sph, int* cnt, int32_t rho0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int L = V.L, M2 = 2 * L;
-    const int y0 = it.y, z0 = it.z, tz = it.w & 0xFFFF;
+    const int y0 = it.y, z0 = it.z, tz = it.w & 0xFFFF, TY = it.w >> 17;
     const int ty = min(TY, L - y0);
     const int RW = strip_rw(L), SLOT = strip_slot(TY, L);
-    // this lane's stencil offsets k = sub + 8j: buffer delta dzc*SLOT + dyc*RW + dx
-    // (15 bits, biased), dyc + 2 (3 bits), shell (3 bits); one word per b
-    const int sub = tid & (kLanesPerSite - 1);
-    uint32_t P0[8], P1[8];
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+    // this lane's stencil offsets k = sub + 8j for sublattice b = warp & 1:
+    // byte delta 4 (dzc*SLOT + dyc*RW + dx) and, 3 bits each, dyc + 2
+    const int sub = lane & 7, b = warp & 1;
+    int Dl[kOffs];
+    uint32_t DY = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int k = sub + kLanesPerSite * j;
+    for (int j = 0; j < kOffs; ++j) {
+        const int k = sub + 8 * j;
         const int o = k < kSph ? sph[k] : sph[0];
-        const int dx = off_dx(o), dy = off_dy(o), dz = off_dz(o);
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int dyc = half_floor(b + dy), dzc = half_floor(b + dz);
-            const uint32_t w = (uint32_t)(dzc * SLOT + dyc * RW + dx + 16384) | ((uint32_t)(dyc + 2) << 15) |
-                               ((uint32_t)off_extra(o) << 18);
-            if (b) P1[j] = w; else P0[j] = w;
-        }
+        const int dyc = half_floor(b + off_dy(o)), dzc = half_floor(b + off_dz(o));
+        Dl[j] = 4 * (dzc * SLOT + dyc * RW + off_dx(o));
+        DY |= (uint32_t)(dyc + 2) << (3 * j);
     }
-    // buffer: planes qb .. qb+7 (relative plane index; rel. plane 2 is z0), all pure Fe
-    for (int r = warp; r < kPlanes * ty; r += kStripWarps) {
-        int32_t* row = buf + (r / ty) * SLOT + (r % ty) * RW;
-        for (int c = lane; c < RW; c += 32) row[c] = (c >= kRowPad && c < kRowPad + M2) ? rho0 : 0;
+    const uint32_t k7 = sub < kSph - 56 ? 0u : 1u;    // offset sub + 56 exists iff 0
+    // buffer: planes qb .. qb+7 (relative plane index; rel. plane 2 is z0); the
+    // strip's rows pure Fe, pads and guard rows 0
+    for (int pr = warp; pr < kPlanes * (ty + 2 * kGuard); pr += kStripThreads / 32) {
+        const int p = pr / (ty + 2 * kGuard), br = pr - p * (ty + 2 * kGuard);
+        int32_t* row = buf + p * SLOT + br * RW;
+        const bool own = br >= kGuard && br < ty + kGuard;
+        for (int c = lane; c < RW; c += 32) row[c] = own && c >= kRowPad && c < kRowPad + M2 ? rho0 : 0;
     }
-    // this thread's chunk of the haloed strip (VEC: 16 sites of one row)
-    int my_hr = -1, my_cx = 0, my_y = -1;
-    if (VEC) {
-        const int cpr = M2 / 16;
-        if (tid < (ty + 4) * cpr) {
-            my_hr = tid / cpr;
-            my_cx = tid - my_hr * cpr;
-            int y = y0 - 2 + my_hr;
-            my_y = y < 0 ? y + L : (y >= L ? y - L : y);
-        }
-    }
-    auto plane_of = [&](int rp) { int z = z0 - 2 + rp; return z < 0 ? z + L : (z >= L ? z - L : z); };
-    auto load = [&](int rp, uint4& v) {
-        if (VEC && my_y >= 0) v = *(const uint4*)(V.species + ((size_t)plane_of(rp) * L + my_y) * M2 + 16 * my_cx);
-    };
-    uint4 pre = make_uint4(0, 0, 0, 0);
-    load(0, pre);
-    if (tid < 4) counts[tid] = 0;
-    __syncthreads();
+    // z and y indices in [-2, 2L) wrap with one correction
+    auto wrap = [&](int z) { return z < 0 ? z + L : (z >= L ? z - L : z); };
     const int n_src = tz + 4;
-    int qb = -2;
-    for (int rp = 0; rp < n_src; ++rp) {
-        const uint4 cur = pre;
-        if (rp + 1 < n_src) load(rp + 1, pre);
-        uint32_t* list = lists + (rp & 1) * list_cap;
-        int* cnt = counts + 2 * (rp & 1);
-        strip_append<VEC>(V.species, L, plane_of(rp), y0, ty, cur, my_hr, my_cx, list, list_cap, cnt);
-        __syncthreads();
-        const int pos = rp - qb;                      // 2 .. 5: targets at buffer planes pos-2 .. pos+2
-        // entries of inner rows: every target row lies in the strip
-        const int ni = cnt[0] * kLanesPerSite;
-        for (int t = tid; t < ni; t += kStripThreads) {
-            const uint32_t en = list[t / kLanesPerSite];
-            const int s = en & 7, X = (en >> 3) & 1023, hr = en >> 13;
-            const int u = pos * SLOT + (hr - 2) * RW + X + kRowPad - 16384;
-            const int32_t* cs = cq[s];
-            const bool b = X & 1;
+    // this thread's chunks k: 16 sites of halo row hr_k of plane pl_k of a block
+    // (the same for every block); off = offset of the chunk in its plane
+    const int cpr = M2 / 16;                           // 16-byte chunks per row (VEC)
+    const int per_plane = (ty + 4) * cpr;
+    int ck_pl[kChunks], ck_hr[kChunks], ck_u[kChunks], ck_off[kChunks];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j == 7 && sub + kLanesPerSite * j >= kSph) break;
-                const uint32_t w = b ? P1[j] : P0[j];
-                atomicAdd(buf + (u + (int)(w & 0x7FFF)), cs[w >> 18]);
-            }
-        }
-        // entries of edge rows: row check
-        const int ne = cnt[1] * kLanesPerSite;
-        for (int t = tid; t < ne; t += kStripThreads) {
-            const uint32_t en = list[list_cap - 1 - t / kLanesPerSite];
-            const int s = en & 7, X = (en >> 3) & 1023, hr = en >> 13;
-            const int u = pos * SLOT + (hr - 2) * RW + X + kRowPad - 16384;
-            const int hm = hr - 4;                    // target row hr + dyc - 2 = hm + (dyc + 2)
-            const int32_t* cs = cq[s];
-            const bool b = X & 1;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j == 7 && sub + kLanesPerSite * j >= kSph) break;
-                const uint32_t w = b ? P1[j] : P0[j];
-                if ((unsigned)(hm + (int)((w >> 15) & 7)) < (unsigned)ty)
-                    atomicAdd(buf + (u + (int)(w & 0x7FFF)), cs[w >> 18]);
-            }
-        }
-        if (tid < 2) counts[2 * ((rp + 1) & 1) + tid] = 0;
-        __syncthreads();
-        if (pos == kShift + 1) {                      // buffer planes 0..3 complete
-            strip_shift<VEC>(V, buf, SLOT, RW, ty, y0, z0, qb, tz, rho0);
-            qb += kShift;
-        }
+    for (int k = 0; k < kChunks; ++k) {
+        const int c = tid + k * kStripThreads;
+        const int pl = VEC ? c / per_plane : 0, rem = c - pl * per_plane;
+        const int hr = VEC ? rem / cpr : 0, cx = rem - hr * cpr;
+        ck_pl[k] = pl;
+        ck_hr[k] = hr;
+        ck_u[k] = (pl + 2) * SLOT + hr * RW + 16 * cx + kRowPad;
+        ck_off[k] = wrap(y0 - 2 + hr) * M2 + 16 * cx;
     }
-    // flush: every source plane is done; the planes still to be written (at
-    // most 3: the last shift came after source plane tz or later) sit in
-    // buffer planes 0..3
-    strip_shift<VEC>(V, buf, SLOT, RW, ty, y0, z0, qb, tz, rho0);
+    uint4 v[kChunks];
+    auto load_block = [&](int rb) {
+        const int nb = min(kBlk, n_src - rb);
+#pragma unroll
+        for (int k = 0; k < kChunks; ++k)
+            if (ck_pl[k] < nb)
+                v[k] = __ldcs((const uint4*)(V.species + (size_t)wrap(z0 - 2 + rb + ck_pl[k]) * L * M2 + ck_off[k]));
+    };
+    if (VEC) load_block(0);
+    if (tid < 4) cnt[tid] = 0;
+    __syncthreads();
+    int qb = -2;
+    for (int rb = 0; rb < n_src; rb += kBlk, qb += kBlk) {
+        const int nb = min(kBlk, n_src - rb);
+        // a. append
+        if (VEC) {
+#pragma unroll
+            for (int k = 0; k < kChunks; ++k) {
+                if (ck_pl[k] >= nb) break;
+                uint32_t M = nonzero_bytes(v[k]);
+                if (!M) continue;
+                const int hr = ck_hr[k];
+                const bool own = strip_own(hr, ty);
+                const uint32_t M0 = M & 0x5555u, M1 = M & 0xAAAAu;
+                int a0 = M0 ? atomicAdd(&cnt[own ? 0 : 1], __popc(M0)) : 0;
+                int a1 = M1 ? atomicAdd(&cnt[own ? 2 : 3], __popc(M1)) : 0;
+                while (M) {
+                    const int j = __ffs(M) - 1;
+                    M &= M - 1;
+                    const uint32_t wj = j < 8 ? (j < 4 ? v[k].x : v[k].y) : (j < 12 ? v[k].z : v[k].w);
+                    const uint32_t en = strip_entry((wj >> (8 * (j & 3))) & 0xFFu, ck_u[k] + j, hr);
+                    if (j & 1) strip_push(lists, en, 1, own, a1++);
+                    else strip_push(lists, en, 0, own, a0++);
+                }
+            }
+            if (rb + kBlk < n_src) load_block(rb + kBlk);   // next block, in flight during the scatter
+        } else {
+            const int n = nb * (ty + 4) * M2;
+            for (int c = tid; c < n; c += kStripThreads) {
+                const int pl = c / ((ty + 4) * M2), rem = c - pl * (ty + 4) * M2, hr = rem / M2, X = rem - hr * M2;
+                const uint32_t sp = V.species[((size_t)wrap(z0 - 2 + rb + pl) * L + wrap(y0 - 2 + hr)) * M2 + X];
+                if (sp != 0) {
+                    const bool own = strip_own(hr, ty);
+                    const int bb = X & 1;
+                    const int at = atomicAdd(&cnt[2 * bb + (own ? 0 : 1)], 1);
+                    strip_push(lists, strip_entry(sp, (pl + 2) * SLOT + hr * RW + X + kRowPad, hr), bb, own, at);
+                }
+            }
+        }
+        __syncthreads();
+        // b. scatter
+        const bool ovf = cnt[0] + cnt[1] > kStripCap || cnt[2] + cnt[3] > kStripCap;   // uniform
+        if (!ovf) {
+            const uint32_t* lst = lists + b * kStripCap;
+            const int first = (warp >> 1) * 4 + (lane >> 3);   // 16 entries per pass and sublattice
+            const int ni = cnt[2 * b], ne = cnt[2 * b + 1];
+            for (int i = first; i < ni; i += 16) {
+                const uint32_t en = lst[i];
+                const uint32_t ub = sbuf + 4 * ((en >> 3) & 0xFFFFFu);
+                const int4 w0 = wt[en & 7][sub][0], w1 = wt[en & 7][sub][1];
+                const int ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int j = 0; j < kOffs - 1; ++j) red_add(ub + Dl[j], ww[j]);
+                red_add_if(ub + Dl[kOffs - 1], ww[kOffs - 1], k7, 1u);
+            }
+            for (int i = first; i < ne; i += 16) {
+                const uint32_t en = lst[kStripCap - 1 - i];
+                const uint32_t ub = sbuf + 4 * ((en >> 3) & 0xFFFFFu);
+                const uint32_t hm = (en >> 23) - 4u;            // target row hr + dyc - 2 = hm + (dyc + 2)
+                const int4 w0 = wt[en & 7][sub][0], w1 = wt[en & 7][sub][1];
+                const int ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int j = 0; j < kOffs; ++j) {
+                    const uint32_t row = j == kOffs - 1 && k7 ? 0xFFFFFFFFu : hm + ((DY >> (3 * j)) & 7);
+                    red_add_if(ub + Dl[j], ww[j], row, (uint32_t)ty);
+                }
+            }
+        } else {
+            // direct scatter of the block, one source site per thread and pass
+            const int n = nb * (ty + 4) * M2;
+            for (int c = tid; c < n; c += kStripThreads) {
+                const int pl = c / ((ty + 4) * M2), rem = c - pl * (ty + 4) * M2, hr = rem / M2, X = rem - hr * M2;
+                uint32_t sp = V.species[((size_t)wrap(z0 - 2 + rb + pl) * L + wrap(y0 - 2 + hr)) * M2 + X];
+                if (sp == 0) continue;
+                sp = sp > 7 ? 7 : sp;
+                const int bb = X & 1, u = (pl + 2) * SLOT + hr * RW + X + kRowPad;
+                for (int k = 0; k < kSph; ++k) {
+                    const int o = sph[k];
+                    const int dyc = half_floor(bb + off_dy(o)), dzc = half_floor(bb + off_dz(o));
+                    if ((unsigned)(hr + dyc - 2) < (unsigned)ty)
+                        atomicAdd(buf + u + dzc * SLOT + dyc * RW + off_dx(o), strip_w(wt, sp, k));
+                }
+            }
+        }
+        __syncthreads();
+        // c. pads of planes 0..3 into their row ends; planes 4..7's pads move down
+        for (int t = tid; t < kBlk * ty * 2; t += kStripThreads) {
+            const int i = t / (2 * ty), rem = t - i * 2 * ty, r = rem >> 1;
+            int32_t* row = buf + i * SLOT + (r + kGuard) * RW;
+            int32_t* up = row + kBlk * SLOT;
+            if ((rem & 1) == 0) {             // sites 0..2 collect the right pads (X = 2L .. 2L+2)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) row[kRowPad + k] += row[kRowPad + M2 + k];
+#pragma unroll
+                for (int k = 0; k < kRowPad; ++k) {
+                    row[kRowPad + M2 + k] = up[kRowPad + M2 + k];
+                    up[kRowPad + M2 + k] = 0;
+                }
+            } else {                          // sites 2L-3..2L-1 collect the left pads (X = -3 .. -1)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) row[kRowPad + M2 - 3 + k] += row[kRowPad - 3 + k];
+#pragma unroll
+                for (int k = 0; k < kRowPad; ++k) {
+                    row[k] = up[k];
+                    up[k] = 0;
+                }
+            }
+        }
+        __syncthreads();
+        // d. shift: planes 0..3 are complete
+        if (VEC) {
+            const int4 pure = make_int4(rho0, rho0, rho0, rho0);
+#pragma unroll
+            for (int i = 0; i < kBlk; ++i) {
+                const int q = qb + i;
+                const bool wr = q >= 2 && q < tz + 2;
+                int4* out = (int4*)(V.rho + ((size_t)(z0 + q - 2) * L + y0) * M2);
+                for (int r = warp; r < ty; r += kStripThreads / 32) {
+                    int4* row = (int4*)(buf + i * SLOT + (r + kGuard) * RW + kRowPad);
+                    int4* up = (int4*)((int32_t*)row + kBlk * SLOT);
+                    int4* orow = out + r * (M2 / 4);
+                    for (int c = lane; c < M2 / 4; c += 32) {
+                        const int4 val = row[c];
+                        if (wr) __stcs(orow + c, val);
+                        row[c] = up[c];
+                        up[c] = pure;
+                    }
+                }
+            }
+        } else {
+            for (int f = tid; f < kBlk * ty * M2; f += kStripThreads) {
+                const int i = f / (ty * M2), rem = f - i * (ty * M2), r = rem / M2, X = rem - r * M2;
+                int32_t* row = buf + i * SLOT + (r + kGuard) * RW + kRowPad;
+                const int q = qb + i;
+                if (q >= 2 && q < tz + 2) V.rho[((size_t)(z0 + q - 2) * L + y0 + r) * M2 + X] = row[X];
+                row[X] = row[X + kBlk * SLOT];
+                row[X + kBlk * SLOT] = rho0;
+            }
+        }
+        if (tid < 4) cnt[tid] = 0;
+        __syncthreads();
+    }
 }
 
-__global__ void __launch_bounds__(kStripThreads) density_strip_kernel(const VoxelDev* vox, const ModelDev* M,
-                                                                      const Tables* tab, const int4* items, int TY,
-                                                                      int buf_ints, int list_cap) {
+__global__ void __launch_bounds__(kStripThreads, 2) density_strip_kernel(const VoxelDev* vox, const ModelDev* M,
+                                                                         const Tables* tab, const int4* items) {
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ int32_t s_cq[8][8];
+    __shared__ int4 s_wt[8][8][2];      // [species][sub]: f_s - f_Fe at the 8 offsets k = sub + 8j
     __shared__ int32_t s_sph[64];
     __shared__ int s_count[4];
     const int4 it = items[blockIdx.x];
     const int tid = threadIdx.x;
     if (tid < kSph) s_sph[tid] = tab->sph_off[tid];
-    if (tid < 64) s_cq[tid / 8][tid % 8] = tid < 40 ? M->cq[tid / 8][tid % 8] : 0;
     __syncthreads();
-    int32_t* buf = (int32_t*)sm;
-    uint32_t* lists = (uint32_t*)(sm + sizeof(int32_t) * (size_t)buf_ints);
+    for (int i = tid; i < 8 * 8 * 8; i += kStripThreads) {
+        const int sp = i >> 6, sub = (i >> 3) & 7, j = i & 7, k = sub + 8 * j;
+        ((int32_t*)s_wt)[i] = (sp >= 1 && sp <= 4 && k < kSph) ? M->cq[sp][off_extra(s_sph[k])] : 0;
+    }
+    __syncthreads();
     const VoxelDev& V = vox[it.x];
-    if (it.w >> 16)
-        strip_body<true>(V, it, TY, buf, lists, list_cap, s_cq, s_sph, s_count, M->rho_pure);
+    const int TY = it.w >> 17;
+    int32_t* buf = (int32_t*)sm;
+    uint32_t* lists = (uint32_t*)(sm + sizeof(int32_t) * (size_t)kPlanes * strip_slot(TY, V.L));
+    if ((it.w >> 16) & 1)
+        strip_body<true>(V, it, buf, lists, s_wt, s_sph, s_count, M->rho_pure);
     else
-        strip_body<false>(V, it, TY, buf, lists, list_cap, s_cq, s_sph, s_count, M->rho_pure);
+        strip_body<false>(V, it, buf, lists, s_wt, s_sph, s_count, M->rho_pure);
 }
 
+int density_strip_rows(int L) { return strip_rows(L); }
+size_t density_strip_smem(int L) { return strip_smem(strip_rows(L), L); }
+
 cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
-                           int n_tiles, const int4* strips, int n_strips, int strip_ty, int strip_lmax,
-                           cudaStream_t st) {
+                           int n_tiles, const int4* strips, int n_strips, size_t strip_dyn, cudaStream_t st) {
     if (n_strips > 0) {
-        const int buf_ints = kPlanes * strip_slot(strip_ty, strip_lmax);
-        const int list_cap = (strip_ty + 4) * 2 * strip_lmax;
-        const size_t dyn = sizeof(int32_t) * (size_t)buf_ints + 2 * sizeof(uint32_t) * (size_t)list_cap;
         cudaError_t e = cudaFuncSetAttribute((const void*)density_strip_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_dyn);
         if (e != cudaSuccess) return e;
-        density_strip_kernel<<<n_strips, kStripThreads, dyn, st>>>(vox, M, tab, strips, strip_ty, buf_ints,
-                                                                   list_cap);
+        density_strip_kernel<<<n_strips, kStripThreads, strip_dyn, st>>>(vox, M, tab, strips);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

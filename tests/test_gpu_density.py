@@ -101,3 +101,16 @@ def test_density_tile_kernel_large_voxel(model):
     for s in sites:
         assert int(rho[s]) == o.rho_fixed(int(s)), s
     b.close()
+
+
+def test_density_dense_lattices_overflow_path(model):
+    # Locally dense lattices: more than 1024 non-Fe sites of one sublattice in a
+    # block of 4 haloed planes sends the block through the direct scatter.
+    descs = [_d(64, 4, (0.10, 0.10, 0.10), uid=20),    # 16-byte path, ~30 % non-Fe
+             _d(48, 4, (0.25, 0.15, 0.10), uid=21),    # 16-byte path, 16-row strips of 48 rows
+             _d(33, 2, (0.30, 0.10, 0.10), uid=22),    # byte path
+             _d(72, 3, (0.002, 0.01, 0.01), uid=23),   # 8-row strips, dilute
+             _d(80, 3, (0.20, 0.10, 0.10), uid=24)]    # 8-row strips, dense
+    b = Batch(descs, model)
+    _check_all(b, descs, model, range(len(descs)))
+    b.close()
