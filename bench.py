@@ -54,10 +54,12 @@ EAM_BYTES_PER_EVENT = 145 * (1 + 4) + 2 + 78 * 4 * 2
 RATE_BYTES_PER_SITE = 5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per event of one
 # full-size step-kernel launch, from one ncu capture of
-# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (536 MB read +
-# 5.36 GB written for 2.56e8 events); valid only for the kernel source it was
-# taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": "def9523bf838cd29265b41eb81e212507f18818c", "bytes_per_event": 23.03}
+# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (534 MB read +
+# 5.36 GB written for 2.56e8 events), and warp instructions per event
+# (smsp__inst_executed.sum of the 2000-event case of the same workload);
+# valid only for the kernel source they were taken from.
+NCU_STEP_TRAFFIC = {"k_step_sha1": "2d47da0abd55060bce182ecb3e8cbfe7bc1dd763", "bytes_per_event": 23.03,
+                    "warp_inst_per_event": 4374}
 
 
 def _step_src_sha1():
@@ -275,9 +277,15 @@ def main():
     value = events_total / dev_time
     peak, peak_kind = _peaks()
     achieved_gbs = EAM_BYTES_PER_EVENT * float(E) * N_VOX * args.steps / sum(times) / 1e9
-    traffic = None
+    traffic, issue = None, None
     if NCU_STEP_TRAFFIC["k_step_sha1"] == _step_src_sha1() and NCU_STEP_TRAFFIC["bytes_per_event"]:
         traffic = NCU_STEP_TRAFFIC["bytes_per_event"] * float(E) * N_VOX
+        # instruction-issue roof: 4 schedulers per SM, one warp instruction per cycle each
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_issue = n_sm * 4 * ((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6
+        ach_issue = value / world * NCU_STEP_TRAFFIC["warp_inst_per_event"]
+        issue = {"warp_inst_per_event": NCU_STEP_TRAFFIC["warp_inst_per_event"], "achieved": ach_issue,
+                 "peak": peak_issue, "unit": "warp instructions/s", "frac": ach_issue / peak_issue}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps, "higher_is_better": True,
@@ -289,7 +297,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "step_kernel (persistent, one CTA per voxel)",
                      "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "bytes_per_event": EAM_BYTES_PER_EVENT,
+                     "bytes_per_event": EAM_BYTES_PER_EVENT, "issue": issue,
                      "note": "latency-bound: each voxel is one serial event chain"},
         "gpu_launches": args.steps,
         "clocks": clocks,
