@@ -188,6 +188,17 @@ akmc_status akmc_step_sublattice_async(akmc_batch* batch, int32_t voxel, uint64_
                                        uint32_t n_supersteps, int32_t sector_cells, double window_s,
                                        akmc_stream stream);
 
+/* Failure-detection test hook for the asynchronous form: runs supersteps
+ * 0 .. n_supersteps-1 like akmc_step_sublattice_async, except that sector
+ * stall_sector is never processed and never reports readiness, so the bounded
+ * waits of its neighbours run out: the voxel's status becomes AKMC_ETIMEOUT
+ * (read with akmc_sync_status) after a few seconds and the device stays usable.
+ * The voxel's state is then unspecified.  AKMC_EINVAL for a sector index out
+ * of range, otherwise as akmc_step_sublattice_async. */
+akmc_status akmc_test_sublattice_stall(akmc_batch* batch, int32_t voxel, uint32_t n_supersteps,
+                                       int32_t sector_cells, double window_s, int32_t stall_sector,
+                                       akmc_stream stream);
+
 /* Re-seed n voxel slots in place with new descriptors (continuous batching:
  * a finished request's slot takes the next request).  Each new descriptor
  * must keep the slot's L, n_vac, model and precision; T, composition, seed

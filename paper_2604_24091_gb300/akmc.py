@@ -70,6 +70,7 @@ def load_library():
             "akmc_step_n": (I32, [P, P, P]),
             "akmc_step_sublattice": (I32, [P, I32, U64, ctypes.c_uint32, I32, ctypes.c_double, P]),
             "akmc_step_sublattice_async": (I32, [P, I32, U64, ctypes.c_uint32, I32, ctypes.c_double, P]),
+            "akmc_test_sublattice_stall": (I32, [P, I32, ctypes.c_uint32, I32, ctypes.c_double, I32, P]),
             "akmc_read_state": (I32, [P, I32, ctypes.POINTER(StateC), P]),
             "akmc_load_state": (I32, [P, I32, P, P, ctypes.c_double, ctypes.c_double, U64, P]),
             "akmc_sync_status": (I32, [P, P, P]),
@@ -225,6 +226,11 @@ class Batch:
         fn = self._lib.akmc_step_sublattice_async if asynchronous else self._lib.akmc_step_sublattice
         _check(fn(self._h, int(voxel), int(superstep0), int(n_supersteps), int(sector_cells), float(window),
                   _stream_ptr(stream)))
+
+    def test_sublattice_stall(self, voxel, n_supersteps, sector_cells, window, stall_sector, stream=None):
+        """Failure-detection hook: one sector never reports readiness (the voxel ends AKMC_ETIMEOUT)."""
+        _check(self._lib.akmc_test_sublattice_stall(self._h, int(voxel), int(n_supersteps), int(sector_cells),
+                                                    float(window), int(stall_sector), _stream_ptr(stream)))
 
     def set_targets(self, n_events, stream=None):
         arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))

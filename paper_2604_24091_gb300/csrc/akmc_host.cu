@@ -292,11 +292,14 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
     Lo.targets = take(sizeof(uint64_t) * n + sizeof(int32_t) * n);   // targets then order
     Lo.order = Lo.targets + sizeof(uint64_t) * n;
     Lo.ident = take(sizeof(int32_t) * n);   // 0, 1, ..., n-1: single-voxel kernel lists
+    int nv_max = 1;
     for (int32_t v = 0; v < n; ++v) {
         const int ns = d[v].L / 8;
         Lo.sl_max_sectors = std::max(Lo.sl_max_sectors, ns * ns * ns);
+        nv_max = std::max(nv_max, d[v].n_vac);
     }
-    Lo.sl_done = take(sizeof(int32_t) * (4 + (size_t)Lo.sl_max_sectors));   // abort word, then done[]
+    // sublattice words: abort word (+3 spare), done[sectors], then stale[vacancies]
+    Lo.sl_done = take(sizeof(int32_t) * (4 + (size_t)Lo.sl_max_sectors + (size_t)nv_max));
     if (has_eam) {
         Lo.phi_raw = take(sizeof(double) * 20 * m->n_r);
         Lo.f_raw = take(sizeof(double) * 8 * m->n_r);
@@ -694,55 +697,63 @@ akmc_status sl_check(akmc_batch* b, int32_t voxel, int32_t Sc, double window_s) 
 }
 }  // namespace
 
-akmc_status akmc_step_sublattice_async(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
-                                       int32_t sector_cells, double window_s, akmc_stream stream) {
-    akmc_status st = sl_check(b, voxel, sector_cells, window_s);
+namespace {
+// Both sublattice forms.  skip_sector >= 0 only with the asynchronous form (test hook).
+akmc_status sl_run(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps, int32_t Sc,
+                   double window_s, bool asynchronous, int skip_sector, cudaStream_t s) {
+    akmc_status st = sl_check(b, voxel, Sc, window_s);
     if (st != AKMC_OK) return st;
     if (n_supersteps == 0) return AKMC_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     if (b->dirty) {
         st = rebuild(b, s);
         if (st != AKMC_OK) return st;
     }
     const BatchArgs a = b->args();
-    const int ns = b->desc[voxel].L / sector_cells, n_sec = ns * ns * ns;
+    const int ns = b->desc[voxel].L / Sc, n_sec = ns * ns * ns;
     int32_t* words = (int32_t*)(b->base + b->lo.sl_done);
-    AKMC_CUDA(cudaMemsetAsync(words, 0, sizeof(int32_t) * (4 + (size_t)n_sec), s));
-    int grid = 0;
-    cudaError_t e = launch_sublattice_async(a, voxel, (uint32_t)superstep0, n_supersteps, sector_cells, n_sec,
-                                            window_s, words + 4, words, b->n_sm, &grid, s);
-    if (e != cudaSuccess) return fail(AKMC_ECUDA, "asynchronous sublattice kernel: %s", cudaGetErrorString(e));
-    e = launch_rebuild(a, 8, (const int32_t*)(b->base + b->lo.ident) + voxel, 1, s);
-    if (e != cudaSuccess) return fail(AKMC_ECUDA, "rebuild kernel: %s", cudaGetErrorString(e));
-    return AKMC_OK;
-}
-
-akmc_status akmc_step_sublattice(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
-                                 int32_t sector_cells, double window_s, akmc_stream stream) {
-    {
-        akmc_status st0 = sl_check(b, voxel, sector_cells, window_s);
-        if (st0 != AKMC_OK) return st0;
-    }
-    const int L = b->desc[voxel].L, Sc = sector_cells;
-    if (n_supersteps == 0) return AKMC_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (b->dirty) {
-        akmc_status st = rebuild(b, s);
-        if (st != AKMC_OK) return st;
-    }
-    const BatchArgs a = b->args();
-    cudaError_t e = sl_prepare(a);
-    if (e != cudaSuccess) return fail(AKMC_ECUDA, "sublattice kernel attribute: %s", cudaGetErrorString(e));
-    const int ns = L / Sc;
-    for (uint32_t i = 0; i < n_supersteps; ++i) {
-        e = launch_sublattice(a, voxel, (uint32_t)(superstep0 + i), Sc, ns * ns * ns, window_s, s);
-        if (e != cudaSuccess) return fail(AKMC_ECUDA, "sublattice kernel: %s", cudaGetErrorString(e));
+    int32_t* stale = words + 4 + b->lo.sl_max_sectors;
+    // stored rates are current here (kept by the step kernel, rebuilt after a load)
+    AKMC_CUDA(cudaMemsetAsync(words, 0, sizeof(int32_t) * (4 + (size_t)b->lo.sl_max_sectors + b->desc[voxel].n_vac), s));
+    cudaError_t e;
+    if (asynchronous) {
+        int grid = 0;
+        e = launch_sublattice_async(a, voxel, (uint32_t)superstep0, n_supersteps, Sc, n_sec, window_s, words + 4,
+                                    words, stale, skip_sector, b->n_sm, &grid, s);
+        if (e != cudaSuccess) return fail(AKMC_ECUDA, "asynchronous sublattice kernel: %s", cudaGetErrorString(e));
+    } else {
+        e = sl_prepare(a);
+        if (e != cudaSuccess) return fail(AKMC_ECUDA, "sublattice kernel attribute: %s", cudaGetErrorString(e));
+        for (uint32_t i = 0; i < n_supersteps; ++i) {
+            e = launch_sublattice(a, voxel, (uint32_t)(superstep0 + i), Sc, n_sec, window_s, stale, s);
+            if (e != cudaSuccess) return fail(AKMC_ECUDA, "sublattice kernel: %s", cudaGetErrorString(e));
+        }
     }
     // the supersteps keep lattice, densities, positions, clock and counter; the
     // voxel's rates and tree are rebuilt from the new lattice
     e = launch_rebuild(a, 8, (const int32_t*)(b->base + b->lo.ident) + voxel, 1, s);
     if (e != cudaSuccess) return fail(AKMC_ECUDA, "rebuild kernel: %s", cudaGetErrorString(e));
     return AKMC_OK;
+}
+}  // namespace
+
+akmc_status akmc_step_sublattice_async(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
+                                       int32_t sector_cells, double window_s, akmc_stream stream) {
+    return sl_run(b, voxel, superstep0, n_supersteps, sector_cells, window_s, true, -1, (cudaStream_t)stream);
+}
+
+akmc_status akmc_step_sublattice(akmc_batch* b, int32_t voxel, uint64_t superstep0, uint32_t n_supersteps,
+                                 int32_t sector_cells, double window_s, akmc_stream stream) {
+    return sl_run(b, voxel, superstep0, n_supersteps, sector_cells, window_s, false, -1, (cudaStream_t)stream);
+}
+
+akmc_status akmc_test_sublattice_stall(akmc_batch* b, int32_t voxel, uint32_t n_supersteps, int32_t sector_cells,
+                                       double window_s, int32_t stall_sector, akmc_stream stream) {
+    if (b && voxel >= 0 && voxel < b->n && sector_cells > 0) {
+        const int ns = b->desc[voxel].L / sector_cells;
+        if (stall_sector < 0 || stall_sector >= ns * ns * ns)
+            return fail(AKMC_EINVAL, "stall_sector %d out of range", stall_sector);
+    }
+    return sl_run(b, voxel, 0, n_supersteps, sector_cells, window_s, true, stall_sector, (cudaStream_t)stream);
 }
 
 akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_voxel_desc* descs, int32_t n,

@@ -33,16 +33,18 @@ int step_occupancy(int warps, int max_nv, int max_P, int win);
 // Synchronous sublattice supersteps of one voxel: sl_prepare sets the kernel's
 // shared-memory limit (once per call sequence, outside any capture);
 // launch_sublattice runs superstep k over n_sectors = (L/sector_cells)^3 CTAs.
+// stale[nv] (zeroed by the caller at the start of a call sequence) tracks which
+// vacancies' stored rates are out of date.
 cudaError_t sl_prepare(const BatchArgs& a);
 cudaError_t launch_sublattice(const BatchArgs& a, int vid, uint32_t k, int sector_cells, int n_sectors,
-                              double window, cudaStream_t st);
+                              double window, int32_t* stale, cudaStream_t st);
 // Asynchronous form: n supersteps from k0 in one cooperative launch of
 // min(n_sectors, resident CTAs) CTAs with per-sector readiness counters
-// done[n_sectors] (zeroed by the caller) and an abort word; grid_out gets the
-// grid size.
+// done[n_sectors] (zeroed by the caller) and an abort word; skip_sector >= 0
+// (test hook) leaves one sector unprocessed; grid_out gets the grid size.
 cudaError_t launch_sublattice_async(const BatchArgs& a, int vid, uint32_t k0, uint32_t n, int sector_cells,
-                                    int n_sectors, double window, int32_t* done, int32_t* abort_flag, int n_sm,
-                                    int* grid_out, cudaStream_t st);
+                                    int n_sectors, double window, int32_t* done, int32_t* abort_flag,
+                                    int32_t* stale, int skip_sector, int n_sm, int* grid_out, cudaStream_t st);
 
 const Tables& host_tables();   // stencil tables built on the host
 void set_last_error(const char* msg);   // text returned by akmc_last_error() on this thread

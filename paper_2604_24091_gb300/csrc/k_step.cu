@@ -95,6 +95,7 @@ struct __align__(16) StepShared {
     // sublattice superstep (see sl_kernel): counter words of the uniforms,
     // octant bounds (cells) and the octant's clock and window
     int32_t sl_on, sl_k, sl_sid, sl_n, sl_nvtot, sl_etab;
+    int32_t* sl_stale;                // per vacancy: stored rates out of date (global)
     int32_t sl_x0, sl_y0, sl_z0, sl_h;
     double sl_t, sl_T;
 };
@@ -117,13 +118,16 @@ struct Dyn {
     int32_t* dprev;   // window path: density change of the last hop, [8 dirs][4 atoms][145 read-set sites]
     int32_t* gslot;   // sublattice superstep: voxel slot of each local vacancy
     int32_t* on;      // sublattice superstep: local vacancy still in the active octant
+    int32_t* apos;    // sublattice superstep: packed half-unit coordinates of every vacancy at the start
+    int32_t* lmap;    // sublattice superstep: local index of every vacancy, -1 if not local
+    int32_t* fr;      // sublattice superstep: local vacancy's stored rates are current
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Offsets of the dynamic shared-memory arrays (16-byte aligned).
 struct DynLayout {
-    size_t off[17];
+    size_t off[20];
     size_t total;
 };
 
@@ -131,7 +135,7 @@ __host__ __device__ inline int win_sites(int W);
 
 __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) {
     const size_t nw = win > 0 ? (size_t)win_sites(win) : 0;
-    const size_t sz[17] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
+    const size_t sz[20] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
                            sizeof(double) * 8 * max_nv, sizeof(double) * 8 * max_nv,
                            sizeof(double) * kEtab,      sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
@@ -139,10 +143,12 @@ __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) 
                            sizeof(int32_t) * max_nv,    (size_t)8 * max_nv,
                            nw,                          sizeof(int32_t) * nw,
                            win > 0 ? sizeof(int32_t) * kEamU * 32 : 0,
-                           sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv};
+                           sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
+                           sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
+                           sizeof(int32_t) * max_nv};
     DynLayout l;
     size_t o = 0;
-    for (int i = 0; i < 17; ++i) {
+    for (int i = 0; i < 20; ++i) {
         l.off[i] = o;
         o = align16(o + sz[i]);
     }
@@ -170,6 +176,9 @@ __device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P,
     d.dprev = win > 0 ? (int32_t*)(base + l.off[14]) : nullptr;
     d.gslot = (int32_t*)(base + l.off[15]);
     d.on = (int32_t*)(base + l.off[16]);
+    d.apos = (int32_t*)(base + l.off[17]);
+    d.lmap = (int32_t*)(base + l.off[18]);
+    d.fr = (int32_t*)(base + l.off[19]);
     return d;
 }
 
@@ -1359,6 +1368,19 @@ __device__ void run_events_sl(StepShared& S, const Dyn& D) {
         if (tid == 0) S.stop = !sl_select(S, D);
         __syncthreads();
         if (S.stop) break;
+        // vacancies outside this sector's list whose read set the hop may change
+        // (within `reach` half units of w): their stored rates go out of date
+        if (tid >= 32) {
+            for (int q = tid - 32; q < S.sl_nvtot; q += NW * 32 - 32) {
+                if (D.lmap[q] >= 0) continue;
+                const int a = D.apos[q];
+                int ddx = (a & 1023) - S.wX, ddy = ((a >> 10) & 1023) - S.wY, ddz = (a >> 20) - S.wZ;
+                ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
+                ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
+                ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
+                if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach) S.sl_stale[q] = 1;
+            }
+        }
         if (fast) {
             phase_fill<NW, MODE>(S);
             __syncthreads();
@@ -1430,10 +1452,14 @@ __device__ uint64_t sl_sector(StepShared& S, const Dyn& D, const Tables* tab, ui
             bool in = false;
             if (q < nv) {
                 const int s = __ldcg(S.v.vac_pos + q), c = s >> 1, bit = s & 1;
-                in = sl_inside(S, 2 * (c % L) + bit, 2 * ((c / L) % L) + bit, 2 * (c / (L * L)) + bit);
+                const int X = 2 * (c % L) + bit, Y = 2 * ((c / L) % L) + bit, Z = 2 * (c / (L * L)) + bit;
+                in = sl_inside(S, X, Y, Z);
+                D.apos[q] = X | (Y << 10) | (Z << 20);
             }
             const unsigned m = __ballot_sync(0xffffffffu, in);
-            if (in) D.gslot[n + __popc(m & ((1u << tid) - 1u))] = q;
+            const int j = n + __popc(m & ((1u << tid) - 1u));
+            if (in) D.gslot[j] = q;
+            if (q < nv) D.lmap[q] = in ? j : -1;
             n += __popc(m);
         }
         if (tid == 0) S.sl_n = n;
@@ -1457,8 +1483,32 @@ __device__ uint64_t sl_sector(StepShared& S, const Dyn& D, const Tables* tab, ui
         D.disp[3 * j + 1] = __ldcg(S.v.vac_disp + 3 * q + 1);
         D.disp[3 * j + 2] = __ldcg(S.v.vac_disp + 3 * q + 2);
         D.on[j] = 1;
+        D.fr[j] = !__ldcg(S.sl_stale + q);
     }
     for (int i = tid; i < 2 * P; i += NT) D.tree[i] = 0.0;
+    __syncthreads();
+    // vacancies whose stored rates are current: rates, sums and leaf from memory
+    for (int i = tid; i < 8 * n_act; i += NT) {
+        const int j = i >> 3, q = D.gslot[j];
+        if (!D.fr[j]) continue;
+        D.rates[i] = __ldcg(S.v.rates + 8 * q + (i & 7));
+        D.dE[i] = __ldcg(S.v.dE + 8 * q + (i & 7));
+        D.hop_sp[i] = __ldcg(S.v.hop_sp + 8 * q + (i & 7));
+    }
+    __syncthreads();
+    for (int j = tid; j < n_act; j += NT) {
+        if (!D.fr[j]) continue;
+        const double* g = D.rates + 8 * j;
+        double* h = D.hsum + 8 * j;
+        h[4] = g[0] + g[1];
+        h[5] = g[2] + g[3];
+        h[6] = g[4] + g[5];
+        h[7] = g[6] + g[7];
+        h[2] = h[4] + h[5];
+        h[3] = h[6] + h[7];
+        h[1] = h[2] + h[3];
+        D.tree[P + j] = h[1];
+    }
     __syncthreads();
     if (tid == 0) {
         S.sl_etab = 1;
@@ -1478,6 +1528,7 @@ __device__ uint64_t sl_sector(StepShared& S, const Dyn& D, const Tables* tab, ui
     __syncthreads();
     const int mode = S.v.model == 0 ? 0 : (S.v.precision == 1 ? 1 : 2);
     for (int j = 0; j < n_act; ++j) {
+        if (D.fr[j]) continue;   // uniform
         if (mode == 0)
             refresh_full<NW, 0>(S, D, j);
         else if (mode == 1)
@@ -1485,26 +1536,46 @@ __device__ uint64_t sl_sector(StepShared& S, const Dyn& D, const Tables* tab, ui
         else
             refresh_full<NW, 2>(S, D, j);
     }
+    // inner nodes from the final leaves, level by level (each node = left + right)
+    if (tid < 32) {
+        for (int lv = P >> 1; lv >= 1; lv >>= 1) {
+            for (int n = lv + tid; n < 2 * lv; n += 32) D.tree[n] = D.tree[2 * n] + D.tree[2 * n + 1];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
     if (mode == 0)
         run_events_sl<NW, 0>(S, D);
     else if (mode == 1)
         run_events_sl<NW, 1>(S, D);
     else
         run_events_sl<NW, 2>(S, D);
+    // the vacancies still inside the octant have current rates (refreshed after
+    // every hop that could change them); those that left it may not
     for (int j = tid; j < n_act; j += NT) {
         const int q = D.gslot[j];
         S.v.vac_pos[q] = D.pos[j];
         S.v.vac_disp[3 * q + 0] = D.disp[3 * j + 0];
         S.v.vac_disp[3 * q + 1] = D.disp[3 * j + 1];
         S.v.vac_disp[3 * q + 2] = D.disp[3 * j + 2];
+        S.sl_stale[q] = D.on[j] ? 0 : 1;
+    }
+    for (int i = tid; i < 8 * n_act; i += NT) {
+        const int q = D.gslot[i >> 3];
+        if (!D.on[i >> 3]) continue;
+        S.v.rates[8 * q + (i & 7)] = D.rates[i];
+        S.v.dE[8 * q + (i & 7)] = D.dE[i];
+        S.v.hop_sp[8 * q + (i & 7)] = D.hop_sp[i];
     }
     return S.n;
 }
 
 // Voxel state for the sublattice kernels: the voxel record, no event log,
-// L2-only lattice loads.  Returns false (uniform) if the voxel is not OK.
+// L2-only lattice loads; stale[q] != 0 marks vacancy q's stored rates (rates,
+// dE, hop species in the voxel record) as out of date.  Returns false
+// (uniform) if the voxel is not OK.
 template <int NW>
-__device__ bool sl_begin(StepShared& S, const BatchArgs& a, int vid) {
+__device__ bool sl_begin(StepShared& S, const BatchArgs& a, int vid, int32_t* stale) {
     load_model<NW>(S, a.model);
     if (threadIdx.x == 0) {
         S.v = a.vox[vid];
@@ -1512,6 +1583,7 @@ __device__ bool sl_begin(StepShared& S, const BatchArgs& a, int vid) {
         S.v.log_cap = 0;
         S.sl_on = 1;
         S.sl_etab = 0;
+        S.sl_stale = stale;
     }
     __syncthreads();
     return S.v.status == kOK;
@@ -1533,12 +1605,13 @@ __device__ __forceinline__ void sl_clock(VoxelDev* gv, double t_hi, double t_lo,
 // Synchronous form: superstep k of voxel `vid`, one CTA per sector (grid
 // (L/Sc)^3); the kernel boundary is the global barrier between supersteps.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint32_t k, int Sc, double T) {
+__global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint32_t k, int Sc, double T,
+                                                     int32_t* stale) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     __shared__ StepShared S;
     const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
     VoxelDev* gv = &a.vox[vid];
-    if (!sl_begin<NW>(S, a, vid)) return;
+    if (!sl_begin<NW>(S, a, vid, stale)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) sl_clock(gv, S.v.t_hi, S.v.t_lo, T * 0.125, 1);
     const uint64_t made = sl_sector<NW>(S, D, a.tab, k, blockIdx.x, Sc, T);
     if (threadIdx.x == 0) {
@@ -1558,7 +1631,9 @@ __global__ void __launch_bounds__(NW * 32) sl_kernel(BatchArgs a, int vid, uint3
 // sectors drift apart freely.  All CTAs are resident (cooperative launch),
 // and the smallest unfinished task always has its inputs ready, so the waits
 // end; each wait is still bounded (a few seconds), after which the voxel gets
-// kETIMEOUT and every CTA leaves at its next wait.
+// kETIMEOUT and every CTA leaves at its next wait.  skip_sector >= 0 (a test
+// hook) names a sector that is never processed nor reported, so that its
+// neighbours' waits run out.
 __device__ __forceinline__ int ld_acquire(const int32_t* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -1595,18 +1670,20 @@ __device__ bool sl_wait(const int32_t* done, int32_t* abort_flag, int sid, int n
 
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) sl_async_kernel(BatchArgs a, int vid, uint32_t k0, uint32_t n, int Sc,
-                                                           double T, int32_t* done, int32_t* abort_flag) {
+                                                           double T, int32_t* done, int32_t* abort_flag,
+                                                           int32_t* stale, int skip_sector) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     __shared__ StepShared S;
     __shared__ int go;
     const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, 0);
     VoxelDev* gv = &a.vox[vid];
-    if (!sl_begin<NW>(S, a, vid)) return;
+    if (!sl_begin<NW>(S, a, vid, stale)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) sl_clock(gv, S.v.t_hi, S.v.t_lo, T * 0.125, n);
     const int ns = S.v.L / Sc, n_sec = ns * ns * ns;
     uint64_t made = 0;
     for (uint32_t i = 0; i < n; ++i) {
         for (int sid = blockIdx.x; sid < n_sec; sid += gridDim.x) {
+            if (sid == skip_sector) continue;   // uniform
             if (threadIdx.x < 32) {
                 const bool ok = sl_wait(done, abort_flag, sid, ns, (int)i, gv);
                 if (threadIdx.x == 0) go = ok;
@@ -1735,14 +1812,15 @@ cudaError_t sl_prepare(const BatchArgs& a) {
 }
 
 cudaError_t launch_sublattice(const BatchArgs& a, int vid, uint32_t k, int sector_cells, int n_sectors,
-                              double window, cudaStream_t st) {
-    sl_kernel<8><<<n_sectors, 256, step_dyn_smem(a.max_nv, a.max_P, 0), st>>>(a, vid, k, sector_cells, window);
+                              double window, int32_t* stale, cudaStream_t st) {
+    sl_kernel<8><<<n_sectors, 256, step_dyn_smem(a.max_nv, a.max_P, 0), st>>>(a, vid, k, sector_cells, window,
+                                                                             stale);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sublattice_async(const BatchArgs& a, int vid, uint32_t k0, uint32_t n, int sector_cells,
-                                    int n_sectors, double window, int32_t* done, int32_t* abort_flag, int n_sm,
-                                    int* grid_out, cudaStream_t st) {
+                                    int n_sectors, double window, int32_t* done, int32_t* abort_flag,
+                                    int32_t* stale, int skip_sector, int n_sm, int* grid_out, cudaStream_t st) {
     const size_t dyn = step_dyn_smem(a.max_nv, a.max_P, 0);
     cudaError_t e = set_smem<8>((const void*)sl_async_kernel<8>, dyn);
     if (e != cudaSuccess) return e;
@@ -1752,8 +1830,9 @@ cudaError_t launch_sublattice_async(const BatchArgs& a, int vid, uint32_t k0, ui
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = std::min(n_sectors, per_sm * n_sm);
     *grid_out = grid;
-    void* args[] = {(void*)&a, (void*)&vid, (void*)&k0, (void*)&n, (void*)&sector_cells, (void*)&window,
-                    (void*)&done, (void*)&abort_flag};
+    void* args[] = {(void*)&a,      (void*)&vid,    (void*)&k0,         (void*)&n,
+                    (void*)&sector_cells, (void*)&window, (void*)&done, (void*)&abort_flag,
+                    (void*)&stale,  (void*)&skip_sector};
     return cudaLaunchCooperativeKernel((const void*)sl_async_kernel<8>, dim3(grid), dim3(256), args, dyn, st);
 }
 

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2604_24091_gb300 import AkmcError, Batch  # noqa: E402
+from paper_2604_24091_gb300 import AkmcError, Batch, ETIMEOUT  # noqa: E402
 
 SPLIT_DE_TOL = 1e-5
 
@@ -190,3 +190,33 @@ def test_async_equals_sync_large_split(model, Sc):
     assert np.array_equal(bs.read_density(0), ba.read_density(0))
     bs.close()
     ba.close()
+
+
+def test_async_stalled_sector_times_out(model):
+    # Failure detection without a fault: one sector never reports readiness, so
+    # its neighbours' bounded waits run out; the voxel ends AKMC_ETIMEOUT, the
+    # other voxel of the batch is untouched and the device stays usable.
+    P, F = synth.PAIR_MODEL, synth.PREC_FP64
+    descs = [synth.VoxelDesc(32, 8, (0.02, 0, 0), 563.0, P, F, seed=5, uid=1),
+             synth.VoxelDesc(16, 4, (0.02, 0, 0), 563.0, P, F, seed=6, uid=2)]
+    b = Batch(descs, model)
+    o = oracle.Voxel(descs[0], model)
+    T = _window(o, 8, 2.0)
+    with pytest.raises(AkmcError):
+        b.test_sublattice_stall(0, 4, 8, T, 64)            # sector index out of range
+    before = b.read_state(1)
+    b.test_sublattice_stall(0, 4, 8, T, 0)
+    st, per = b.sync_status()
+    assert per[0] == ETIMEOUT and per[1] == 0
+    after = b.read_state(1)
+    assert np.array_equal(before["species"], after["species"]) and after["n_events"] == 0
+    b.close()
+    # a fresh batch runs normally afterwards
+    c = Batch([descs[0]], model)
+    c.step_sublattice(0, 0, 16, 8, T, asynchronous=True)
+    per_o = o.step_sublattice(0, 16, 8, T)
+    g = c.read_state(0)
+    assert c.sync_status()[0] == 0
+    assert g["n_events"] == per_o.sum()
+    assert np.array_equal(g["species"], o.state()["species"])
+    c.close()
