@@ -58,7 +58,7 @@ RATE_BYTES_PER_SITE = 5
 # 5.36 GB written for 2.56e8 events), and warp instructions per event
 # (smsp__inst_executed.sum of the 2000-event case of the same workload);
 # valid only for the kernel source they were taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": "2d47da0abd55060bce182ecb3e8cbfe7bc1dd763", "bytes_per_event": 23.03,
+NCU_STEP_TRAFFIC = {"k_step_sha1": "0f4331c64c48b342f3b81b5792a389fb4d92f540", "bytes_per_event": 23.03,
                     "warp_inst_per_event": 4374}
 
 
@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--launch", default=None, help="warps,ctas_per_sm of the step kernel (skips the tuner)")
     ap.add_argument("--rate-kernel", action="store_true",
                     help="run only the rate-kernel leg (300 EAM voxels of 64^3 cells) and print its JSON")
+    ap.add_argument("--sublattice", action="store_true",
+                    help="run only the large-voxel sublattice leg (128^3 cells, 64 vacancies) and print its JSON")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload (Poisson arrivals, continuous batching) instead")
     args = ap.parse_args()
@@ -222,6 +224,12 @@ def main():
         torch.cuda.set_device(0)
         peak, peak_kind = _peaks()
         print(json.dumps(rate_kernel_leg(synth.default_model(), torch, peak, peak_kind, Batch)), flush=True)
+        return
+    if args.sublattice:
+        import torch
+        from paper_2604_24091_gb300 import Batch
+        torch.cuda.set_device(0)
+        print(json.dumps(sublattice_leg(synth.default_model(), torch, Batch)), flush=True)
         return
 
     import torch

@@ -1691,7 +1691,8 @@ __global__ void __launch_bounds__(NW * 32) sl_async_kernel(BatchArgs a, int vid,
             __syncthreads();
             if (!go) goto out;   // uniform
             made += sl_sector<NW>(S, D, a.tab, k0 + i, sid, Sc, T);
-            __threadfence();
+            // every thread's writes precede the barrier; thread 0's release store
+            // (cumulative over them) publishes the sector's progress
             __syncthreads();
             if (threadIdx.x == 0) {
                 if (S.v.status != kOK) {
