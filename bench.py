@@ -433,7 +433,16 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
         ub.step(np.minimum(tg, 200).astype(np.uint64))
         tu = _time_region(lambda: ub.step(tg), torch)
         stu, _ = ub.sync_status()
-        out[key] = {"value": float(tg.sum()) / tu, "unit": UNIT, "status": stu,
+        extra = {}
+        if key == "large":   # the Cu-cluster histogram taken every 1e6 events of this configuration
+            ub.cluster_hist(0)
+            th = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                ub.cluster_hist(0)
+                th.append(time.perf_counter() - t0)
+            extra = {"cluster_hist_ms": 1e3 * min(th), "events_between_histograms": 1000000}
+        out[key] = {"value": float(tg.sum()) / tu, "unit": UNIT, "status": stu, **extra,
                     "config": ("1000 voxels, L in {16,24,32,48,64}, 1-8 vacancies, pair/EAM 50/50, "
                                "1e4 events per vacancy" if key == "uneven" else
                                "1 voxel of 128^3 cells, 64 vacancies, EAM split, 2e4 events")}
