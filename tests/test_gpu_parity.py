@@ -336,3 +336,25 @@ def test_large_voxel_fp64_trajectory(model):
     _assert_rates(g["rates"], so["rates"])
     assert abs(_time(g) - _time(so)) <= 1e-12 * _time(so)
     b.close()
+
+
+def test_max_vacancies_bit_exact(model):
+    # 256 vacancies (the largest count a voxel may hold): the rate tree has 256
+    # leaves and every hop refreshes many neighbours
+    P, E, F = synth.PAIR_MODEL, synth.EAM_MODEL, synth.PREC_FP64
+    descs = [synth.VoxelDesc(16, 256, (0.03, 0.02, 0.02), 563.0, P, F, seed=77, uid=5),
+             synth.VoxelDesc(16, 256, (0.03, 0.02, 0.02), 563.0, E, F, seed=78, uid=6)]
+    n = [5000, 500]
+    b = Batch(descs, model, event_log_capacity=max(n))
+    b.step(np.array(n, np.uint64))
+    assert b.sync_status()[0] == 0
+    for v, d in enumerate(descs):
+        o = oracle.Voxel(d, model)
+        log_o = o.step(n[v], log=True)
+        g = b.read_state(v, log=True)
+        so = o.state()
+        assert np.array_equal(g["event_log"][:n[v]], log_o), v
+        assert np.array_equal(g["species"], so["species"])
+        assert np.array_equal(g["vac_disp"], so["vac_disp"])
+        _assert_rates(g["rates"], so["rates"])
+    b.close()

@@ -146,6 +146,7 @@ def test_fp64_eam_larger_voxel_bit_exact(model):
 
 @pytest.mark.parametrize("mdl,prec,L,Sc,nv", [(synth.PAIR_MODEL, synth.PREC_FP64, 16, 8, 12),
                                                (synth.PAIR_MODEL, synth.PREC_FP64, 24, 8, 30),
+                                               (synth.PAIR_MODEL, synth.PREC_FP64, 32, 8, 256),
                                                (synth.EAM_MODEL, synth.PREC_FP64, 32, 8, 24)])
 def test_async_readiness_matches_oracle(model, mdl, prec, L, Sc, nv):
     # one cooperative launch with per-sector readiness: the same result as the

@@ -41,6 +41,9 @@ def test_workspace_bytes_sizes_and_validation(lib, model):
         A.workspace_bytes(bad, model)
     with pytest.raises(A.AkmcError):
         A.workspace_bytes([synth.VoxelDesc(4, 0, (0, 0, 0), 563.0, 0)], model)    # no vacancy
+    A.workspace_bytes([synth.VoxelDesc(16, 256, (0, 0, 0), 563.0, 0)], model)  # the most vacancies allowed
+    with pytest.raises(A.AkmcError):
+        A.workspace_bytes([synth.VoxelDesc(16, 257, (0, 0, 0), 563.0, 0)], model)  # one more
     with pytest.raises(A.AkmcError):
         A.workspace_bytes([synth.VoxelDesc(4, 1, (0.6, 0.6, 0), 563.0, 0)], model)  # over-full
     m = copy.deepcopy(model)
