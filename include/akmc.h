@@ -323,7 +323,7 @@ const char* akmc_last_error(void);               /* thread-local, never NULL */
  * caller's scratch (256-byte aligned device memory, bytes >= the size above);
  * returns the number of parts in *n_parts; synchronises the stream.  The plan
  * stays valid for any number of akmc_select_logits calls with the same offsets.
- * akmc_select_logits: stream-ordered (three kernels, no host synchronisation,
+ * akmc_select_logits: stream-ordered (two kernels, no host synchronisation,
  * capturable in a CUDA graph).  Outputs (device, n_seg entries): out_index[s] =
  * offset of the selected logit within segment s, or -1 if the segment has no
  * admissible logit; out_logp[s] = log of its probability (float32; NaN if none).

@@ -63,6 +63,22 @@ def test_segments_of_every_shape(tau):
     assert ties <= 2
 
 
+def test_aligned_segments_with_ragged_parts():
+    # segment starts on 16-logit boundaries: parts are staged by bulk copies,
+    # with the last partial 16 bytes of logits and mask read directly
+    rng = np.random.default_rng(5)
+    lens = [16, 32, 8192, 8208, 16432, 1040, 8192 * 3 + 48, 64, 23]
+    offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n = int(offsets[-1])
+    logits = rng.normal(0.0, 2.5, n).astype(np.float32)
+    mask = (rng.random(n) < 0.5).astype(np.uint8)
+    ties = 0
+    for counter in range(6):
+        ties += _compare(logits, offsets, 0.8, 77, counter, mask)
+        ties += _compare(logits, offsets, 1.3, 78, counter, None)
+    assert ties <= 2
+
+
 def test_all_masked_and_single_entry():
     logits = np.array([1.0, 2.0, -np.inf, 5.0, 0.5, 0.25], np.float32)
     mask = np.array([0, 0, 1, 1, 0, 0], np.uint8)
