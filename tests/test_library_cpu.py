@@ -6,6 +6,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 import synth
@@ -65,3 +67,20 @@ def test_oracle_and_library_share_no_source():
     for f in ("akmc_oracle.cpp", "akmc_oracle.h", "__init__.py"):
         text = open(os.path.join(ROOT, "oracle", f)).read()
         assert "akmc_device" not in text and "paper_2604_24091_gb300" not in text
+
+
+def test_select_plan_sizing_and_validation(lib):
+    # host-side planning of the global selection (no device needed): parts of
+    # up to 8192 logits per segment, invalid offsets rejected with 0 bytes
+    L = A.load_library()
+
+    def nbytes(off):
+        a = np.asarray(off, np.int64)
+        return L.akmc_select_scratch_bytes(A._ptr(a), len(a) - 1)
+
+    one = nbytes([0, 8192])
+    assert one > 0
+    assert nbytes([0, 8192 * 200 + 1]) > one                # 201 parts
+    assert nbytes([0, 0, 5, 5]) > 0                        # empty segments are allowed
+    assert nbytes([0, 5, 3]) == 0                          # decreasing
+    assert nbytes([0, (1 << 30) + 1]) == 0                 # longer than 2^30 logits
