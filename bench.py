@@ -54,12 +54,12 @@ EAM_BYTES_PER_EVENT = 145 * (1 + 4) + 2 + 78 * 4 * 2
 RATE_BYTES_PER_SITE = 5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per event of one
 # full-size step-kernel launch, from one ncu capture of
-# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (534 MB read +
-# 5.36 GB written for 2.56e8 events), and warp instructions per event
+# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (696 MB read +
+# 5.39 GB written for 2.56e8 events), and warp instructions per event
 # (smsp__inst_executed.sum of the 2000-event case of the same workload);
 # valid only for the kernel source they were taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": "0f4331c64c48b342f3b81b5792a389fb4d92f540", "bytes_per_event": 23.03,
-                    "warp_inst_per_event": 4374}
+NCU_STEP_TRAFFIC = {"k_step_sha1": "59c1ee62c3adf61a031e4b08f32b3c1e1822b2ed", "bytes_per_event": 23.79,
+                    "warp_inst_per_event": 4196}
 
 
 def _step_src_sha1():

@@ -96,6 +96,7 @@ struct __align__(16) StepShared {
     // octant bounds (cells) and the octant's clock and window
     int32_t sl_on, sl_k, sl_sid, sl_n, sl_nvtot, sl_etab;
     int32_t* sl_stale;                // per vacancy: stored rates out of date (global)
+    int32_t wrot;                     // window path: rotation of the warp roles (threads)
     int32_t sl_x0, sl_y0, sl_z0, sl_h;
     double sl_t, sl_T;
 };
@@ -972,7 +973,9 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
     constexpr int WPH = NW / 8;                                     // warps per hop
     constexpr int NE = MODE == 0 ? kPairE : kEamE;                  // entries per hop
     constexpr int EJ = (NE + 32 * WPH - 1) / (32 * WPH);            // entries per lane
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // roles by rotated thread index: a second CTA on the SM puts its warp 0
+    // (the float64 chain of phase A) on another sub-partition (see sm_rotation)
+    const int tid = (threadIdx.x + S.wrot) & (NT - 1), lane = tid & 31, warp = tid >> 5;
     const int L = S.v.L, M2 = 2 * L;
     if (tid == 0) {
         S.W = L < kWinMax ? L : kWinMax;
@@ -1265,12 +1268,26 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
     flush_clock<NW>(S);
 }
 
+// Warps of an SM are spread over its 4 sub-partitions by warp slot; two CTAs
+// resident on one SM would put both warps 0, and so both float64 chains of the
+// window path, on the same sub-partition and its float64 pipe.  The CTAs that
+// arrive on an SM alternate between two rotations of the warp roles (0 and 2
+// warps), counted per SM since the library was loaded.
+__device__ unsigned int g_sm_arrivals[1024];
+
+__device__ __forceinline__ int sm_rotation() {
+    unsigned int sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    return (atomicAdd(&g_sm_arrivals[sm & 1023u], 1u) & 1u) ? 64 : 0;
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) step_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     __shared__ StepShared S;
     const Dyn D = carve(dyn_raw, a.max_nv, a.max_P, a.win);
     load_model<NW>(S, a.model);
+    if (threadIdx.x == 0) S.wrot = sm_rotation();
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) {
