@@ -11,7 +11,11 @@
 // proportional to the total rate (Sec. "Current State of the Art"); rates are
 // Arrhenius (Eq. 8); inadmissible transitions are masked out and all events
 // compete globally (Eq. 1-2); voxels are periodic and independent
-// (Sec. "Mesoscopic Voxel-Parallel Formulation").
+// (Sec. "Mesoscopic Voxel-Parallel Formulation").  The synchronous sublattice
+// schedule (orc_step_sublattice; Sec. "Asynchronous Sublattice Parallelism"
+// names its synchronous form and the readiness refinement) runs the sectors of
+// each superstep one after another; it is pinned by sector-order independence,
+// conservation, the clock and the pure-Fe scheduled walk (test_oracle_sublattice).
 #include "akmc_oracle.h"
 
 #include <algorithm>
