@@ -106,7 +106,9 @@ def test_density_tile_kernel_large_voxel(model):
 def test_density_dense_lattices_overflow_path(model):
     # Locally dense lattices: more than 1024 non-Fe sites of one sublattice in a
     # block of 4 haloed planes sends the block through the direct scatter.
-    descs = [_d(64, 4, (0.10, 0.10, 0.10), uid=20),    # 16-byte path, ~30 % non-Fe
+    descs = [_d(64, 4, (0.30, 0.30, 0.20), uid=25),    # 16-byte path, 80 % non-Fe
+             _d(33, 2, (0.30, 0.30, 0.20), uid=26),    # byte path, 80 % non-Fe
+             _d(64, 4, (0.10, 0.10, 0.10), uid=20),    # 16-byte path, ~30 % non-Fe
              _d(48, 4, (0.25, 0.15, 0.10), uid=21),    # 16-byte path, 16-row strips of 48 rows
              _d(33, 2, (0.30, 0.10, 0.10), uid=22),    # byte path
              _d(72, 3, (0.002, 0.01, 0.01), uid=23),   # 8-row strips, dilute
