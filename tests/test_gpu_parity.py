@@ -358,3 +358,35 @@ def test_max_vacancies_bit_exact(model):
         assert np.array_equal(g["vac_disp"], so["vac_disp"])
         _assert_rates(g["rates"], so["rates"])
     b.close()
+
+
+@pytest.mark.parametrize("mdl,prec", [(synth.PAIR_MODEL, synth.PREC_FP64), (synth.EAM_MODEL, synth.PREC_FP64),
+                                      (synth.EAM_MODEL, synth.PREC_SPLIT)])
+def test_arrhenius_temperature_sensitivity_on_gpu(model, mdl, prec):
+    # Eq. 9 on the GPU's rate tables: one alloy state at T (1 +- 1e-5) in three voxels;
+    # d ln(rate)/dT = Ea / (kB T^2) with Ea from the GPU's own dE and hop species.
+    L, T, h = 6, 563.0, 563.0 * 1e-5
+    sp, vac = synth.random_lattice(L, 4, (0.08, 0.05, 0.05), seed=23)
+    descs = [synth.VoxelDesc(L, 4, (0, 0, 0), Tx, mdl, prec, seed=1, uid=1) for Tx in (T - h, T, T + h)]
+    b = Batch(descs, model)
+    for v in range(3):
+        b.load_state(v, sp, vac)
+    b.compute_rates()
+    g = [b.read_state(v) for v in range(3)]
+    rates = [x["rates"].reshape(-1, 8) for x in g]
+    dE = g[1]["dE"].reshape(-1, 8)
+    A = np.zeros_like(dE, dtype=np.int64)
+    for q, s in enumerate(vac):
+        c, bb = s >> 1, s & 1
+        X, Y, Z = 2 * (c % L) + bb, 2 * ((c // L) % L) + bb, 2 * (c // (L * L)) + bb
+        for d in range(8):
+            Xn, Yn, Zn = ((X + (-1 if d & 1 else 1)) % (2 * L), (Y + (-1 if d & 2 else 1)) % (2 * L),
+                          (Z + (-1 if d & 4 else 1)) % (2 * L))
+            A[q, d] = sp[((((Zn >> 1) * L + (Yn >> 1)) * L + (Xn >> 1)) << 1) | (Xn & 1)]
+    E0 = np.asarray(model.E0)
+    live = A != 4
+    Ea = np.maximum(0.0, np.maximum(dE, E0[np.minimum(A, 3)] + dE / 2))
+    slope = (np.log(rates[2][live]) - np.log(rates[0][live])) / (2 * h)
+    np.testing.assert_allclose(slope, Ea[live] / (synth.KB_EV * T * T), rtol=1e-6)
+    assert (rates[1][~live] == 0).all()
+    b.close()

@@ -236,3 +236,39 @@ def test_density_brute_force(model):
                 rho[i] += int(fq[sp[j]][k])
     np.testing.assert_array_equal(v.rho_all(), rho)
     assert all(v.rho_fixed(i) == rho[i] for i in range(0, N, 7))
+
+
+def _hop_atoms(species, vac_pos, L):
+    """Species at each vacancy's 8 first-neighbour hop targets (dir = (dx<0) + 2(dy<0) + 4(dz<0))."""
+    out = np.zeros((len(vac_pos), 8), np.int64)
+    for q, s in enumerate(vac_pos):
+        b, c = s & 1, s >> 1
+        X, Y, Z = 2 * (c % L) + b, 2 * ((c // L) % L) + b, 2 * (c // (L * L)) + b
+        for d in range(8):
+            dx, dy, dz = (-1 if d & 1 else 1), (-1 if d & 2 else 1), (-1 if d & 4 else 1)
+            Xn, Yn, Zn = (X + dx) % (2 * L), (Y + dy) % (2 * L), (Z + dz) % (2 * L)
+            out[q, d] = species[((((Zn >> 1) * L + (Yn >> 1)) * L + (Xn >> 1)) << 1) | (Xn & 1)]
+    return out
+
+
+@pytest.mark.parametrize("mdl", [0, 1])
+def test_arrhenius_temperature_sensitivity(model, mdl):
+    # Eq. 9: d ln(rate)/dT = Ea / (kB T^2) with Ea = max(0, dE, E0(A) + dE/2), checked by a
+    # central difference of the rates of one alloy state at T (1 +- 1e-5).
+    L, T, h = 6, 563.0, 563.0 * 1e-5
+    sp, vac = synth.random_lattice(L, 4, (0.08, 0.05, 0.05), seed=23)
+    rates = {}
+    for Tx in (T - h, T, T + h):
+        v = oracle.Voxel(synth.VoxelDesc(L, 4, (0, 0, 0), Tx, mdl, 0, seed=1, uid=1), model)
+        v.load(sp, vac)
+        st = v.state()
+        rates[Tx] = st["rates"].reshape(-1, 8)
+        if Tx == T:
+            dE = st["dE"].reshape(-1, 8)
+    A = _hop_atoms(sp, vac, L)
+    E0 = np.asarray(model.E0)
+    live = A != 4
+    Ea = np.maximum(0.0, np.maximum(dE, E0[np.minimum(A, 3)] + dE / 2))
+    slope = (np.log(rates[T + h][live]) - np.log(rates[T - h][live])) / (2 * h)
+    np.testing.assert_allclose(slope, Ea[live] / (KB * T * T), rtol=1e-6)
+    assert (rates[T][~live] == 0).all()
