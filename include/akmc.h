@@ -52,7 +52,7 @@ typedef enum {
     AKMC_EINVAL = 1,    /* invalid argument or descriptor                         */
     AKMC_ENOMEM = 2,    /* workspace smaller than akmc_workspace_bytes()          */
     AKMC_ECUDA = 3,     /* a CUDA runtime call failed (message in last_error)     */
-    AKMC_ETIMEOUT = 4,  /* reserved: a bounded device wait gave up                */
+    AKMC_ETIMEOUT = 4,  /* a bounded device wait gave up (sublattice readiness)  */
     AKMC_ETRAPPED = 5,  /* voxel total rate is 0: no admissible event             */
     AKMC_ENUMERIC = 6   /* density outside the embedding table, or NaN/Inf rate   */
 } akmc_status;
@@ -275,8 +275,11 @@ akmc_status akmc_cluster_hist(akmc_batch* batch, int32_t voxel, int32_t mode,
  * 524,288 sites (L > 64) are rejected with AKMC_EINVAL.  The call allocates
  * nothing: no cudaMalloc, cudaFree or allocating library routine.  Its first
  * call on a device does a one-time set-up there (device addresses of the
- * static arrays and a copy of the neighbour tables into them), so make that
- * first call before any stream capture.  Every call shares the scratch
+ * static arrays and a copy of the neighbour tables into them, waited for
+ * with a device synchronisation so that kernels on any stream see it), so
+ * make that first call before any stream capture.  The set-up is not
+ * repeated after cudaDeviceReset: do not call this entry point on a device
+ * that was reset after its first call.  Every call shares the scratch
  * array, which keeps the last call's contents (each call re-initialises what
  * it needs); calls that overlap on the GPU -- on different streams, or from
  * different host threads -- race on it.  Stream-ordered; does not

@@ -159,10 +159,22 @@ def cluster_hist_noalloc(species, L, mode, hist, stream=None):
     `species` a CUDA uint8 tensor of 2L^3 codes, `hist` a CUDA int64 tensor of
     8 bins that receives the counts (stream-ordered)."""
     import torch
-    assert species.is_cuda and species.dtype == torch.uint8 and species.is_contiguous()
-    assert hist.is_cuda and hist.dtype == torch.int64 and hist.numel() >= 8
-    _check(load_library().akmc_cluster_hist_noalloc(ctypes.c_void_p(species.data_ptr()), int(L), int(mode),
-                                                    ctypes.c_void_p(hist.data_ptr()), _stream_ptr(stream)))
+    L = int(L)
+    if not (isinstance(species, torch.Tensor) and isinstance(hist, torch.Tensor)):
+        raise TypeError("species and hist must be torch tensors")
+    if not (species.is_cuda and species.dtype == torch.uint8 and species.is_contiguous()):
+        raise ValueError("species must be a contiguous CUDA uint8 tensor")
+    if not (hist.is_cuda and hist.dtype == torch.int64 and hist.is_contiguous() and hist.numel() >= 8):
+        raise ValueError("hist must be a contiguous CUDA int64 tensor of at least 8 elements")
+    if L >= 1 and species.numel() < 2 * L ** 3:
+        # the C entry point cannot see the buffer's size: a short buffer would be read past its end
+        raise ValueError("species holds %d codes, fewer than 2L^3 = %d" % (species.numel(), 2 * L ** 3))
+    if species.device != hist.device:
+        raise ValueError("species and hist are on different devices")
+    # the static scratch used is that of the current device: run on the tensors' device
+    with torch.cuda.device(species.device):
+        _check(load_library().akmc_cluster_hist_noalloc(ctypes.c_void_p(species.data_ptr()), L, int(mode),
+                                                        ctypes.c_void_p(hist.data_ptr()), _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):

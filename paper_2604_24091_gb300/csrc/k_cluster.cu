@@ -153,8 +153,15 @@ extern "C" akmc_status akmc_cluster_hist_noalloc(const uint8_t* species, int32_t
             e = cudaGetSymbolAddress((void**)&s.tables, g_static_tables);
             if (e != cudaSuccess)
                 return static_fail(AKMC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            e = cudaMemcpy(s.tables, &host_tables(), sizeof(Tables), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) return static_fail(AKMC_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+            // A copy from pageable host memory may return before the data reach
+            // the device; the kernels run on the caller's stream, which may be a
+            // non-blocking one that nothing orders after this copy, so wait for it.
+            e = cudaMemcpyToSymbol(g_static_tables, &host_tables(), sizeof(Tables));
+            if (e != cudaSuccess)
+                return static_fail(AKMC_ECUDA, std::string("cudaMemcpyToSymbol: ") + cudaGetErrorString(e));
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess)
+                return static_fail(AKMC_ECUDA, std::string("cudaDeviceSynchronize: ") + cudaGetErrorString(e));
             s.done = true;
         }
         su = s;

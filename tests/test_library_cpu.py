@@ -84,3 +84,14 @@ def test_select_plan_sizing_and_validation(lib):
     assert nbytes([0, 0, 5, 5]) > 0                        # empty segments are allowed
     assert nbytes([0, 5, 3]) == 0                          # decreasing
     assert nbytes([0, (1 << 30) + 1]) == 0                 # longer than 2^30 logits
+
+
+def test_noalloc_wrapper_rejects_host_tensors_before_any_call():
+    # the argument checks run on the host before the library is called: host
+    # tensors, a short lattice buffer and a non-tensor are refused without a GPU
+    torch = pytest.importorskip("torch")
+    out = torch.zeros(8, dtype=torch.int64)
+    with pytest.raises(ValueError, match="CUDA uint8"):
+        A.cluster_hist_noalloc(torch.zeros(2 * 4 ** 3, dtype=torch.uint8), 4, 0, out)
+    with pytest.raises(TypeError):
+        A.cluster_hist_noalloc(np.zeros(2 * 4 ** 3, np.uint8), 4, 0, out)
