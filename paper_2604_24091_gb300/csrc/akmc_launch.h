@@ -21,8 +21,17 @@ constexpr int kTX = 32, kTY = 16, kTZ = 16, kHalo = 2;
 constexpr int kStripMaxL = 256;
 int density_strip_rows(int L);
 size_t density_strip_smem(int L);
-cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
-                           int n_tiles, const int4* strips, int n_strips, size_t strip_dyn, cudaStream_t st);
+// Ring strips (voxels with L % 8 == 0, 8 <= L <= 128 and 16-byte aligned
+// species and density arrays): item (voxel, y0, z0, tz) covers rows
+// [y0, y0 + density_ring_rows()) of planes [z0, z0+tz); items are launched in
+// groups of equal L, each with density_ring_smem(L) bytes of dynamic shared memory.
+struct RingGroup { int first, count, L; };
+bool density_ring_ok(int L);
+int density_ring_rows();
+size_t density_ring_smem(int L);
+cudaError_t launch_density(VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles, int n_tiles,
+                           const int4* strips, int n_strips, size_t strip_dyn, const int4* rings,
+                           const RingGroup* groups, int n_groups, cudaStream_t st);
 
 size_t step_dyn_smem(int max_nv, int max_P, int win);
 cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, const int32_t* list,
