@@ -63,6 +63,17 @@ NCU_STEP_TRAFFIC = {"k_step_sha1": "59c1ee62c3adf61a031e4b08f32b3c1e1822b2ed", "
                     "warp_inst_per_event": 4196}
 
 
+# DRAM bytes of one density_strip_kernel launch on the rate-kernel workload (300
+# EAM voxels of 64^3 cells): 167 MB read + 569 MB written, from one ncu capture
+# of `bench.py --rate-kernel`; valid only for the kernel source it was taken from.
+NCU_RATE_TRAFFIC = {"k_density_sha1": "f9c23584f4b6205e6bb666bb96971f85260d47d0", "bytes": 736e6}
+
+
+def _src_sha1(name):
+    p = os.path.join(ROOT, "paper_2604_24091_gb300", "csrc", name)
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()
+
+
 def _step_src_sha1():
     p = os.path.join(ROOT, "paper_2604_24091_gb300", "csrc", "k_step.cu")
     return hashlib.sha1(open(p, "rb").read()).hexdigest()
@@ -212,6 +223,9 @@ def main():
                     help="run only the rate-kernel leg (300 EAM voxels of 64^3 cells) and print its JSON")
     ap.add_argument("--sublattice", action="store_true",
                     help="run only the large-voxel sublattice leg (128^3 cells, 64 vacancies) and print its JSON")
+    ap.add_argument("--large-run", action="store_true",
+                    help="run the large configuration as configured (128^3 cells, 64 vacancies, 1e8 events, "
+                         "Cu-cluster histogram every 1e6 events) and print its JSON")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload (Poisson arrivals, continuous batching) instead")
     args = ap.parse_args()
@@ -225,6 +239,12 @@ def main():
         torch.cuda.set_device(0)
         peak, peak_kind = _peaks()
         print(json.dumps(rate_kernel_leg(synth.default_model(), torch, peak, peak_kind, Batch)), flush=True)
+        return
+    if args.large_run:
+        import torch
+        from paper_2604_24091_gb300 import Batch
+        torch.cuda.set_device(0)
+        print(json.dumps(large_run(synth.default_model(), torch, Batch)), flush=True)
         return
     if args.sublattice:
         import torch
@@ -303,16 +323,25 @@ def main():
         "config": {"workload": workload_name(E),
                    "voxels_per_gpu": N_VOX, "events_per_voxel_per_step": E, "launch": [warps, per_sm],
                    "l2": "flushed between timed steps (256 MB write)", "wall_s_timed_region": t_wall},
-        "roofline": {"bound": "hbm", "kernel": "step_kernel (persistent, one CTA per voxel)",
-                     "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "bytes_per_event": EAM_BYTES_PER_EVENT, "issue": issue,
-                     "note": "latency-bound: each voxel is one serial event chain"},
+        # The step kernel's roof is instruction issue (each voxel is one serial event
+        # chain; its 84 MB working set stays in L2): achieved warp instructions/s
+        # against 4 schedulers per SM at the SM clock.  The HBM fraction is kept
+        # beside it for the contract's algorithmic-bytes view.
+        "roofline": dict(
+            ({"bound": "alu", "achieved": issue["achieved"], "peak": issue["peak"], "unit": issue["unit"],
+              "frac": issue["frac"], "warp_inst_per_event": issue["warp_inst_per_event"],
+              "peak_kind": "152 SMs x 4 schedulers x max SM clock, one warp instruction per cycle each"}
+             if issue else {"bound": "alu", "achieved": None, "peak": None, "unit": "warp instructions/s",
+                            "frac": None}),
+            kernel="step_kernel (persistent, one CTA per voxel)", traffic=traffic,
+            hbm={"achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
+                 "peak_kind": peak_kind, "bytes_per_event": EAM_BYTES_PER_EVENT, "traffic": traffic},
+            note="latency- and issue-bound: each voxel is one serial event chain; DRAM carries ~24 B/event"),
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_extras:
-        line.update(extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch))
+        line.update(extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch, (warps, per_sm)))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -331,9 +360,10 @@ def rate_kernel_leg(model, torch, peak, peak_kind, Batch):
     sites = sum(2 * d.L ** 3 for d in big)
     gbs = RATE_BYTES_PER_SITE * sites / min(ts) / 1e9
     rb.close()
+    traffic = NCU_RATE_TRAFFIC["bytes"] if _src_sha1("k_density.cu") == NCU_RATE_TRAFFIC["k_density_sha1"] else None
     return {"bound": "hbm", "kernel": "akmc_compute_rates (density + rates + trees)",
             "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "traffic": None, "peak_kind": peak_kind,
+            "traffic": traffic, "algorithmic_bytes": RATE_BYTES_PER_SITE * sites, "peak_kind": peak_kind,
             "workload": "300 EAM voxels x 64^3 cells, 157 M sites (> L2)",
             "ms": 1e3 * min(ts)}
 
@@ -356,6 +386,36 @@ def logit_select_leg(torch, dev, peak, peak_kind):
     return {"bound": "hbm", "kernel": "akmc_select_logits (part pass, system search)", "achieved": gbs,
             "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
             "workload": "256 systems x 524288 logits (float32) + mask (uint8), 671 MB", "ms": 1e3 * min(ts)}
+
+
+def large_run(model, torch, Batch, total=100_000_000, every=1_000_000):
+    """The large configuration as configured: one voxel of 128^3 cells
+    (4.19 M sites), 64 vacancies, EAM split precision, global residence-time
+    selection over the device-resident rate tree, run to 1e8 events with the
+    Cu-cluster size histogram (1nn+2nn) taken every 1e6 events.  Events/s
+    counts the stepping time only (CUDA events); the histograms are timed
+    apart."""
+    cfg = synth.config_large()
+    lb = Batch(cfg, model)
+    t_step, t_hist, series, clock = 0.0, 0.0, [], []
+    wall0 = time.perf_counter()
+    for k in range(total // every):
+        t_step += _time_region(lambda: lb.step(every), torch)
+        t0 = time.perf_counter()
+        series.append(lb.cluster_hist(0).tolist())
+        t_hist += time.perf_counter() - t0
+        st = lb.read_state(0, species=False)
+        clock.append(st["t_hi"] + st["t_lo"])
+        if st["status"] != 0:
+            break
+    s = lb.read_state(0, species=False)
+    lb.close()
+    return {"config": "1 voxel of 128^3 cells (4194304 sites), Fe-0.2Cu-0.7Ni-1.4Mn at%, 64 vacancies, EAM split, "
+                      "%d events, Cu-cluster histogram every %d events" % (total, every),
+            "events": s["n_events"], "status": s["status"], "value": s["n_events"] / t_step, "unit": UNIT,
+            "step_seconds": t_step, "histogram_ms_mean": 1e3 * t_hist / max(1, len(series)),
+            "wall_s": time.perf_counter() - wall0, "simulated_time_s": clock[-1] if clock else 0.0,
+            "bins": "1,2,3,4,5-9,10-19,20-49,>=50", "histograms": series, "clock_s": clock}
 
 
 def sublattice_leg(model, torch, Batch, sector_cells=16, n_st=800, windows=(1.0, 4.0)):
@@ -386,7 +446,56 @@ def sublattice_leg(model, torch, Batch, sector_cells=16, n_st=800, windows=(1.0,
     return out
 
 
-def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
+def split_vs_fp64(model, Batch, pairs):
+    """Largest |dE_split - dE_fp64| (eV) and relative rate difference over GPU
+    states of split-precision EAM voxels: every (descriptor, state) pair is
+    loaded into a float64-EAM batch on the GPU (akmc_load_state, then
+    akmc_compute_rates) and the 8 hop energy changes of every vacancy compared."""
+    if not pairs:
+        return None
+    fd = [dataclasses.replace(d, precision=synth.PREC_FP64) for d, _ in pairs]
+    fb = Batch(fd, model)
+    for i, (_, s) in enumerate(pairs):
+        fb.load_state(i, s["species"], s["vac_pos"], s["t_hi"], s["t_lo"], s["n_events"])
+    fb.compute_rates()
+    de, rr, hops = 0.0, 0.0, 0
+    for i, (_, s) in enumerate(pairs):
+        f = fb.read_state(i, species=False)
+        de = max(de, float(np.abs(f["dE"] - s["dE"]).max()))
+        m = f["rates"] > 0
+        if m.any():
+            rr = max(rr, float((np.abs(f["rates"][m] - s["rates"][m]) / f["rates"][m]).max()))
+        hops += int(f["dE"].size)
+    fb.close()
+    return {"max_abs_dE_eV": de, "max_rel_rate_diff": rr, "voxels": len(pairs), "hops": hops,
+            "tolerance_eV": 1e-5, "reference": "float64 EAM path on the GPU (= float64 oracle within 1e-12 eV)"}
+
+
+def uneven_leg(model, torch, Batch, per_vac=100000, replays=10):
+    """The uneven configuration as configured: 1000 voxels, 1e5 events per
+    vacancy, launch shape from the autotuner, advanced by `replays` replays of
+    one captured CUDA graph (each replay: per_vac / replays events per vacancy)."""
+    from paper_2604_24091_gb300 import tune as T
+    cfg = synth.config_uneven(1000)
+    t0 = time.perf_counter()
+    shape = T.tune(cfg, model, events=2000)
+    t_tune = time.perf_counter() - t0
+    ub = Batch(cfg, model)
+    ub.set_launch(*shape)
+    ub.step(np.array([200 * d.n_vac for d in cfg], np.uint64))   # warm-up (not counted)
+    chunk = np.array([per_vac // replays * d.n_vac for d in cfg], np.uint64)
+    g = ub.capture_step(chunk)
+    torch.cuda.synchronize()
+    tu = _time_region(lambda: [g.replay() for _ in range(replays)], torch)
+    stu, _ = ub.sync_status()
+    n = float(chunk.sum()) * replays
+    return {"value": n / tu, "unit": UNIT, "status": stu, "events": n, "seconds": tu,
+            "launch": list(shape), "tune_s": t_tune, "graph_replays": replays,
+            "config": "1000 voxels, L in {16,24,32,48,64}, 1-8 vacancies, pair/EAM 50/50, T 543-593 K, "
+                      "1e5 events per vacancy, autotuned launch shape, CUDA-graph replays"}, ub
+
+
+def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch, launch):
     out = {}
     # end to end through the public API with pinned host buffers: load the
     # lattices, (rebuild), step, read the lattices and clocks back
@@ -425,30 +534,49 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
     p.close()
     out["rate_kernel_roofline"] = rate_kernel_leg(model, torch, peak, peak_kind, Batch)
     out["logit_select_roofline"] = logit_select_leg(torch, dev, peak, peak_kind)
-    # the uneven configuration (1000 voxels, L 16-64, 1-8 vacancies, pair/EAM)
-    # and the large one (128^3 cells, 64 vacancies): events/s of one persistent launch
-    for key, cfg, per_vac in (("uneven", synth.config_uneven(1000), 10000), ("large", synth.config_large(), 20000)):
-        ub = Batch(cfg, model)
-        tg = np.array([per_vac * d.n_vac for d in cfg], np.uint64) if key == "uneven" else \
-            np.full(len(cfg), per_vac, np.uint64)
-        ub.step(np.minimum(tg, 200).astype(np.uint64))
-        tu = _time_region(lambda: ub.step(tg), torch)
-        stu, _ = ub.sync_status()
-        extra = {}
-        if key == "large":   # the Cu-cluster histogram taken every 1e6 events of this configuration
-            ub.cluster_hist(0)
-            th = []
-            for _ in range(3):
-                t0 = time.perf_counter()
-                ub.cluster_hist(0)
-                th.append(time.perf_counter() - t0)
-            extra = {"cluster_hist_ms": 1e3 * min(th), "events_between_histograms": 1000000}
-        out[key] = {"value": float(tg.sum()) / tu, "unit": UNIT, "status": stu, **extra,
-                    "config": ("1000 voxels, L in {16,24,32,48,64}, 1-8 vacancies, pair/EAM 50/50, "
-                               "1e4 events per vacancy" if key == "uneven" else
-                               "1 voxel of 128^3 cells, 64 vacancies, EAM split, 2e4 events")}
-        ub.close()
+    # the uneven configuration as configured: 1000 voxels (L 16-64, 1-8 vacancies,
+    # pair/EAM mixed), 1e5 events per vacancy, the autotuner's launch shape, run as
+    # replays of one captured CUDA graph (10 replays of 1e4 events per vacancy)
+    out["uneven"], ub = uneven_leg(model, torch, Batch)
+    # the large configuration (128^3 cells, 64 vacancies): events/s of one persistent launch
+    lcfg = synth.config_large()
+    lb = Batch(lcfg, model)
+    lb.step(200)
+    tl = _time_region(lambda: lb.step(20000), torch)
+    stl, _ = lb.sync_status()
+    lb.cluster_hist(0)
+    th = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        lb.cluster_hist(0)
+        th.append(time.perf_counter() - t0)
+    out["large"] = {"value": 20000 / tl, "unit": UNIT, "status": stl, "cluster_hist_ms": 1e3 * min(th),
+                    "events_between_histograms": 1000000,
+                    "config": "1 voxel of 128^3 cells, 64 vacancies, EAM split, 2e4 events (the full 1e8-event "
+                              "run with a histogram every 1e6 events: bench.py --large-run)"}
+    # precision: split-precision EAM against the float64 EAM path, per configuration,
+    # on sampled GPU states (the float64 path matches the float64 oracle within 1e-12 eV)
+    prec = {}
+    sample = [0, 37, 101, 150, 203, 255]
+    prec["batched_eam"] = split_vs_fp64(model, Batch, [(descs[v], b.read_state(v)) for v in sample])
+    eam_u = [v for v, d in enumerate(ub.descs) if d.model == synth.EAM_MODEL][:24]
+    prec["uneven_eam"] = split_vs_fp64(model, Batch, [(ub.descs[v], ub.read_state(v)) for v in eam_u])
+    prec["large"] = split_vs_fp64(model, Batch, [(lcfg[0], lb.read_state(0))])
+    ub.close()
+    lb.close()
+    # the batched workload in float64 EAM: events/s beside the split precision
+    f64 = Batch(synth.config_batched_eam(N_VOX, precision=synth.PREC_FP64), model)
+    f64.set_launch(*launch)
+    f64.step(2000)
+    n64 = 100000
+    t64 = _time_region(lambda: f64.step(n64), torch)
+    st64, _ = f64.sync_status()
+    prec["batched_eam_fp64_events_per_s"] = {"value": n64 * N_VOX / t64, "unit": UNIT, "status": st64,
+                                             "events_per_voxel": n64}
+    f64.close()
+    out["precision"] = prec
     out["large_sublattice"] = sublattice_leg(model, torch, Batch)
+    out["serving"], out["precision"]["serving"] = serving_block(model, torch, Batch)
     # the oracle on the host cores, bounded sample of the same workload
     procs = os.cpu_count() or 1
     per = 3 * args.ref_events
@@ -459,49 +587,90 @@ def extras(b, descs, model, torch, dev, n_ev, args, peak, peak_kind, Batch):
     return out
 
 
+def _serve_window(model, torch, duration, policy, rate=200.0, seed=None, precision=None, reserve_slots=2048,
+                  collect_state=False):
+    """Config-5 Poisson window: arrivals at `rate` for `duration` s of 32^3-cell
+    EAM requests (1e6-1e7 events each), 120 GB budget, one reserved pool."""
+    from paper_2604_24091_gb300.serve import Request, Server, latency_summary
+    prec = synth.PREC_SPLIT if precision is None else precision
+    proto = synth.VoxelDesc(32, 1, (0.003, 0.007, 0.014), 563.0, synth.EAM_MODEL, prec)
+    srv = Server(model, hbm_budget=120e9, chunk=20000, policy=policy, reserve=[(proto, reserve_slots)])
+    kw = {} if seed is None else {"seed": seed}
+    reqs = [Request(t, d, n, i) for i, (t, d, n) in
+            enumerate(synth.serving_requests(duration, rate, precision=prec, **kw))]
+    res, st = srv.run(reqs, collect_state=collect_state)
+    for r in res:
+        r.desc = reqs[r.rid].desc
+    out = dict(latency_summary(res), events_per_s=st["events_per_s"], elapsed_s=st["elapsed_s"],
+               requests_offered=len(reqs), offered_events=int(sum(r.n_events for r in reqs)),
+               slots=srv.n_slots, capacity_events_per_s=st["events"] / max(st["busy_s"], 1e-9),
+               statuses=sorted({r.status for r in res}))
+    srv.close()
+    return out, res
+
+
+def serving_ensemble(model, torch, policy, n=384, slots_budget=48e6):
+    """The dynamic voxel scheduling claim (Eq. 10): an ensemble of mixed-shape
+    voxels, each advanced by a simulated-time horizon, all due at once, more
+    requests than slots (HBM budget); makespan and latency with FIFO admission
+    or largest expected work (nu W0 t_sim) first."""
+    from paper_2604_24091_gb300.serve import Request, Server, latency_summary
+    reqs = [Request(0.0, d, t_sim=t, rid=i) for i, (d, t) in enumerate(synth.mixed_requests(n))]
+    srv = Server(model, hbm_budget=slots_budget, chunk=50000, policy=policy, min_pool=8, max_pool=64)
+    res, st = srv.run(reqs, realtime=False)
+    out = dict(latency_summary(res), events=st["events"], events_per_s=st["events_per_s"],
+               elapsed_s=st["elapsed_s"], pools=st["pools"], bytes=st["bytes"], requests=len(reqs),
+               statuses=sorted({r.status for r in res}))
+    srv.close()
+    return out, res
+
+
+def serving_block(model, torch, Batch):
+    """Serving in the default bench line: a 1-s config-5 Poisson window with
+    FIFO and with proxy admission (p50/p99 per 1e6 events), the mixed-shape
+    time-horizon ensemble with both policies, and the split-precision error
+    of served results against the float64 EAM path."""
+    out = {}
+    for pol in ("fifo", "proxy"):
+        out["window_1s_" + pol], res = _serve_window(model, torch, 1.0, pol, collect_state=pol == "fifo")
+        if pol == "fifo":
+            sample = [r for r in res if r.state is not None][:8]
+            prec = split_vs_fp64(model, Batch, [(r.desc, r.state) for r in sample])
+    out["ensemble_fifo"], _ = serving_ensemble(model, torch, "fifo")
+    out["ensemble_proxy"], _ = serving_ensemble(model, torch, "proxy")
+    return out, prec
+
+
 def serving(args):
-    """Serving workload: Poisson arrivals (200 requests/s for 10 s) of
-    batched-EAM-like voxels (32^3 cells, 1 vacancy, split precision), each
+    """Serving workload (config 5): Poisson arrivals (200 requests/s for 10 s)
+    of batched-EAM-like voxels (32^3 cells, 1 vacancy, split precision), each
     asking for 1e6-1e7 events (log-uniform), admitted under a 120 GB HBM
     budget with continuous batching; then the same at 70% of the measured
-    capacity.  Reports p50/p99 latency per 1e6 events and events/s."""
+    capacity, FIFO and proxy admission; the same requests in float64 EAM at
+    70% of its own capacity; and the mixed-shape ensemble.  Reports p50/p99
+    latency per 1e6 events and events/s."""
     import torch
-    from paper_2604_24091_gb300.serve import Request, Server, latency_summary
+    from paper_2604_24091_gb300 import Batch
     torch.cuda.set_device(0)
     model = synth.default_model()
-    shape = synth.VoxelDesc(32, 1, (0.003, 0.007, 0.014), 563.0, synth.EAM_MODEL, synth.PREC_SPLIT)
-    srv = Server(model, shape, hbm_budget=120e9, max_slots=2048, chunk=20000)
     out = {"metric": METRIC + " (serving)", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
            "config": {"workload": "serving: Poisson 200 req/s for 10 s, 32^3-cell EAM voxels, 1e6-1e7 events "
-                      "each, 120 GB HBM budget", "slots": srv.n_slots, "bytes_per_slot": srv.bytes_per_slot,
-                      "chunk_events": srv.chunk}}
-    reqs = [Request(t, d, n, i) for i, (t, d, n) in enumerate(synth.serving_requests(10.0, 200.0))]
-    res, st = srv.run(reqs)
-    out["window"] = dict(latency_summary(res), events_per_s=st["events_per_s"], elapsed_s=st["elapsed_s"],
-                         requests_offered=len(reqs), offered_events=int(sum(r.n_events for r in reqs)))
-    cap = st["events"] / max(st["busy_s"], 1e-9)
-    mean_ev = float(np.mean([r.n_events for r in reqs]))
+                      "each, 120 GB HBM budget"}}
+    out["window"], res = _serve_window(model, torch, 10.0, "fifo")
+    cap = out["window"]["capacity_events_per_s"]
+    mean_ev = 5.5e6
     lam = 0.7 * cap / mean_ev
-    reqs70 = [Request(t, d, n, i) for i, (t, d, n) in
-              enumerate(synth.serving_requests(10.0, lam, seed=synth.SEED_BASE + 15))]
-    res70, st70 = srv.run(reqs70)
-    out["at_70pct_capacity"] = dict(latency_summary(res70), events_per_s=st70["events_per_s"],
-                                    rate_hz=lam, requests=len(reqs70), capacity_events_per_s=cap)
-    # the same requests in FP64 EAM (the reference precision; split-mode energy changes agree with it
-    # within 1e-5 eV): capacity from a saturated offline batch, then arrivals at 70 % of it
-    shape64 = dataclasses.replace(shape, precision=synth.PREC_FP64)
-    srv64 = Server(model, shape64, hbm_budget=120e9, max_slots=2048, chunk=20000)
-    probe = [Request(0.0, dataclasses.replace(d, precision=synth.PREC_FP64), 200000, i)
-             for i, (t, d, n) in enumerate(synth.serving_requests(10.0, 200.0, seed=synth.SEED_BASE + 16)[:srv64.n_slots])]
-    _, stp = srv64.run(probe, realtime=False)
-    cap64 = stp["events"] / max(stp["busy_s"], 1e-9)
-    lam64 = 0.7 * cap64 / mean_ev
-    reqs64 = [Request(t, d, n, i) for i, (t, d, n) in
-              enumerate(synth.serving_requests(10.0, lam64, seed=synth.SEED_BASE + 15, precision=synth.PREC_FP64))]
-    res64, st64 = srv64.run(reqs64)
-    out["fp64_at_70pct_capacity"] = dict(latency_summary(res64), events_per_s=st64["events_per_s"], rate_hz=lam64,
-                                         requests=len(reqs64), capacity_events_per_s=cap64)
-    out["value"] = st["events_per_s"]
+    for pol in ("fifo", "proxy"):
+        out["at_70pct_capacity_" + pol], _ = _serve_window(model, torch, 10.0, pol, rate=lam, seed=synth.SEED_BASE + 15)
+    # float64 EAM: capacity from a saturated window, then arrivals at 70 % of it
+    w64, _ = _serve_window(model, torch, 2.0, "fifo", precision=synth.PREC_FP64)
+    cap64 = w64["capacity_events_per_s"]
+    out["fp64_at_70pct_capacity"], _ = _serve_window(model, torch, 10.0, "fifo", rate=0.7 * cap64 / mean_ev,
+                                                     seed=synth.SEED_BASE + 15, precision=synth.PREC_FP64)
+    out["fp64_at_70pct_capacity"]["capacity_events_per_s"] = cap64
+    for pol in ("fifo", "proxy"):
+        out["ensemble_" + pol], _ = serving_ensemble(model, torch, pol)
+    out["value"] = out["window"]["events_per_s"]
     print(json.dumps(out), flush=True)
 
 

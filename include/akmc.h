@@ -201,8 +201,9 @@ akmc_status akmc_test_sublattice_stall(akmc_batch* batch, int32_t voxel, uint32_
 
 /* Re-seed n voxel slots in place with new descriptors (continuous batching:
  * a finished request's slot takes the next request).  Each new descriptor
- * must keep the slot's L, n_vac, model and precision; T, composition, seed
- * and uid may change.  The slot restarts at event 0 and time 0 with a fresh
+ * must keep the slot's L, n_vac and model; T, composition, precision, seed
+ * and uid may change (a split-precision voxel in a batch created without one
+ * runs the general path: same results, no lattice window).  The slot restarts at event 0 and time 0 with a fresh
  * Philox placement, densities, rate tables, rates and tree; other voxels are
  * untouched.  Stream-ordered with respect to earlier and later launches on
  * the same stream; synchronises the stream before returning. */
@@ -253,6 +254,22 @@ int64_t akmc_batch_vacancies(const akmc_batch* batch);
  * n_voxels entries); returns AKMC_OK if every voxel is OK, else the status
  * of the lowest-indexed voxel that is not. */
 akmc_status akmc_sync_status(akmc_batch* batch, akmc_stream stream, int32_t* per_voxel);
+
+/* Workload proxy of the dynamic voxel scheduling (Sec. "Dynamic Voxel
+ * Scheduling", Eq. 10: W_v ~ M_v exp(-E_v / (kB T_v)), M_v a multiplicity
+ * of local events and E_v an effective barrier set by the voxel's defect
+ * state), evaluated on the device from each voxel's current hop rates:
+ *   M_hat[v] = number of admissible hops (rate > 0) of all its vacancies,
+ *   W[v]     = Gamma_tot / nu (Gamma_tot = sum of its 8 n_vac hop rates),
+ *   E_hat[v] = -kB T_v ln(W[v] / M_hat[v]) eV, the single barrier that gives
+ *              every admissible hop the voxel's mean rate, so that
+ *              W = M_hat exp(-E_hat / (kB T_v)) holds exactly (+inf if M_hat = 0).
+ * Gamma_tot = nu W is the voxel's event rate: advancing it by dt of simulated
+ * time takes about nu W dt events.  In pure Fe, E_hat = E0(Fe) and M_hat = 8
+ * n_vac.  Outputs: host arrays of n_voxels doubles, each nullable.  Rebuilds
+ * rates first after a state load; uses the batch's small I/O area, so it is
+ * stream-ordered with the batch's other calls; synchronises the stream. */
+akmc_status akmc_workload_proxy(akmc_batch* batch, double* W, double* M_hat, double* E_hat, akmc_stream stream);
 
 /* Cu cluster size histogram of one voxel: connected components of Cu under
  * 1nn+2nn (mode 0) or 1nn (mode 1) adjacency; bins {1,2,3,4,5-9,10-19,

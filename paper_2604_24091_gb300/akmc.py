@@ -84,6 +84,7 @@ def load_library():
             "akmc_select_plan": (I32, [P, I32, P, SZ, P, P]),
             "akmc_select_logits": (I32, [P, P, I32, I32, ctypes.c_float, U64, U64, P, P, P, P]),
             "akmc_cluster_hist_noalloc": (I32, [P, I32, I32, P, P]),
+            "akmc_workload_proxy": (I32, [P, P, P, P, P]),
             "akmc_set_launch": (I32, [P, I32, I32]),
             "akmc_n_voxels": (I32, [P]),
             "akmc_destroy_batch": (None, [P]),
@@ -362,6 +363,13 @@ class Batch:
         rho = np.zeros(2 * L ** 3, np.int32)
         _check(self._lib.akmc_read_density(self._h, int(voxel), _ptr(rho), _stream_ptr(stream)))
         return rho
+
+    def workload_proxy(self, stream=None):
+        """Eq. 10 workload proxy of every voxel from its current rates:
+        (W, M_hat, E_hat) arrays, W = Gamma_tot / nu = M_hat exp(-E_hat / kT)."""
+        W, M, E = (np.zeros(self.n, np.float64) for _ in range(3))
+        _check(self._lib.akmc_workload_proxy(self._h, _ptr(W), _ptr(M), _ptr(E), _stream_ptr(stream)))
+        return W, M, E
 
     def cluster_hist(self, voxel, mode=0, stream=None):
         h = np.zeros(8, np.int64)

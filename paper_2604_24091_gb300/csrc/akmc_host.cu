@@ -269,10 +269,8 @@ struct Layout {
     size_t state_begin = 0, state_end = 0, io = 0, reset_list = 0, reset_items = 0;
     size_t b_species = 0, b_pos = 0, b_disp = 0, tot_N = 0, tot_nv = 0;
     std::vector<int4> item_list;       // density tiles (voxels with L > kStripMaxL)
-    std::vector<int4> strip_list;      // density strips (voxels with L <= kStripMaxL, no ring)
-    std::vector<int4> ring_list;       // ring strips (density_ring_ok voxels), sorted by L
-    std::vector<RingGroup> ring_groups;
-    size_t strips = 0, reset_strips = 0, rings = 0, reset_rings = 0;
+    std::vector<int4> strip_list;      // density strips (voxels with L <= kStripMaxL)
+    size_t strips = 0, reset_strips = 0;
     int strip_lmax = 0;
     size_t strip_dyn = 0;              // dynamic shared memory of the strip kernel (batch maximum)
     int max_nv = 1, max_P = 1, win = 0;
@@ -309,21 +307,8 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         Lo.Fd = take(sizeof(Cubic64) * 4 * (m->n_rho - 1));
         Lo.Ff = take(sizeof(float4) * 4 * m->n_rho);   // one zero pad per species at the last knot
         Lo.Fq = take(sizeof(long long) * 4 * m->n_rho);
-        // Offsets of each voxel's species and densities from the (256-byte
-        // aligned) starts of those arrays: ring strips need both on 16 bytes.
-        std::vector<char> ring_v(n, 0);
-        {
-            size_t accN = 0, accR = 0;
-            for (int32_t v = 0; v < n; ++v) {
-                const size_t N = 2 * (size_t)d[v].L * d[v].L * d[v].L;
-                if (d[v].model == AKMC_EAM)
-                    ring_v[v] = density_ring_ok(d[v].L) && accN % 16 == 0 && (4 * accR) % 16 == 0;
-                accN += N;
-                if (d[v].model == AKMC_EAM) accR += N;
-            }
-        }
         for (int32_t v = 0; v < n; ++v) {
-            if (d[v].model != AKMC_EAM || ring_v[v]) continue;
+            if (d[v].model != AKMC_EAM) continue;
             int L = d[v].L;
             if (L <= kStripMaxL) {
                 Lo.strip_lmax = std::max(Lo.strip_lmax, L);
@@ -342,7 +327,7 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
             for (int ci = 0; ci < 5; ++ci) {
                 long long cnt = 0;
                 for (int32_t v = 0; v < n; ++v) {
-                    if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL || ring_v[v]) continue;
+                    if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL) continue;
                     const int L = d[v].L, tz = std::min(cand[ci], L), ty = density_strip_rows(L);
                     cnt += (long long)((L + ty - 1) / ty) * ((L + tz - 1) / tz);
                 }
@@ -352,7 +337,7 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
                 }
             }
             for (int32_t v = 0; v < n; ++v) {
-                if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL || ring_v[v]) continue;
+                if (d[v].model != AKMC_EAM || d[v].L > kStripMaxL) continue;
                 const int L = d[v].L, tz = std::min(tz_cap, L), ty = density_strip_rows(L);
                 Lo.strip_dyn = std::max(Lo.strip_dyn, density_strip_smem(L));
                 for (int z = 0; z < L; z += tz)
@@ -360,38 +345,6 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
                         Lo.strip_list.push_back(make_int4(v, y, z, std::min(tz, L - z) | (ty << 17)));
             }
         }
-        // Ring strips: density_ring_rows() rows each; z extent as for the strips
-        // (>= 1024 items where the batch allows), grouped by L for the launches.
-        {
-            const int ty = density_ring_rows();
-            const int cand[5] = {1 << 30, 64, 32, 16, 8};
-            int tz_cap = 8;
-            for (int ci = 0; ci < 5; ++ci) {
-                long long cnt = 0;
-                for (int32_t v = 0; v < n; ++v)
-                    if (ring_v[v]) cnt += (long long)((d[v].L + ty - 1) / ty) * ((d[v].L + cand[ci] - 1) / cand[ci]);
-                if (cnt >= 1024) {
-                    tz_cap = cand[ci];
-                    break;
-                }
-            }
-            std::vector<int32_t> vs;
-            for (int32_t v = 0; v < n; ++v)
-                if (ring_v[v]) vs.push_back(v);
-            std::stable_sort(vs.begin(), vs.end(), [&](int32_t a, int32_t c) { return d[a].L < d[c].L; });
-            for (int32_t v : vs) {
-                const int L = d[v].L, tz = std::min(tz_cap, L);
-                if (Lo.ring_groups.empty() || Lo.ring_groups.back().L != L)
-                    Lo.ring_groups.push_back(RingGroup{(int)Lo.ring_list.size(), 0, L});
-                for (int z = 0; z < L; z += tz)
-                    for (int y = 0; y < L; y += ty) {
-                        Lo.ring_list.push_back(make_int4(v, y, z, std::min(tz, L - z)));
-                        Lo.ring_groups.back().count++;
-                    }
-            }
-        }
-        Lo.rings = take(sizeof(int4) * std::max<size_t>(1, Lo.ring_list.size()));
-        Lo.reset_rings = take(sizeof(int4) * std::max<size_t>(1, Lo.ring_list.size()));
         Lo.items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
         Lo.reset_items = take(sizeof(int4) * std::max<size_t>(1, Lo.item_list.size()));
         Lo.strips = take(sizeof(int4) * std::max<size_t>(1, Lo.strip_list.size()));
@@ -499,12 +452,10 @@ namespace {
 
 akmc_status rebuild(akmc_batch* b, cudaStream_t st) {
     BatchArgs a = b->args();
-    if (b->lo.has_eam && (!b->lo.item_list.empty() || !b->lo.strip_list.empty() || !b->lo.ring_list.empty())) {
+    if (b->lo.has_eam && (!b->lo.item_list.empty() || !b->lo.strip_list.empty())) {
         cudaError_t e = launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + b->lo.items),
                                        (int)b->lo.item_list.size(), (const int4*)(b->base + b->lo.strips),
-                                       (int)b->lo.strip_list.size(), b->lo.strip_dyn,
-                                       (const int4*)(b->base + b->lo.rings), b->lo.ring_groups.data(),
-                                       (int)b->lo.ring_groups.size(), st);
+                                       (int)b->lo.strip_list.size(), b->lo.strip_dyn, st);
         if (e != cudaSuccess) return fail(AKMC_ECUDA, "density kernel: %s", cudaGetErrorString(e));
     }
     cudaError_t e = launch_rebuild(a, 8, nullptr, 0, st);
@@ -657,9 +608,6 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n, const akm
         if (!lo.strip_list.empty())
             AKMC_TRY(cudaMemcpyAsync(b->base + lo.strips, lo.strip_list.data(),
                                      sizeof(int4) * lo.strip_list.size(), cudaMemcpyHostToDevice, s));
-        if (!lo.ring_list.empty())
-            AKMC_TRY(cudaMemcpyAsync(b->base + lo.rings, lo.ring_list.data(),
-                                     sizeof(int4) * lo.ring_list.size(), cudaMemcpyHostToDevice, s));
     }
     AKMC_TRY(cudaMemsetAsync(b->base + lo.state_begin, 0, lo.state_end - lo.state_begin, s));
     launch_setup_model((ModelDev*)(b->base + lo.model), (int32_t*)(b->base + lo.status), has_eam,
@@ -821,8 +769,10 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
         seen[v] = 1;
         const akmc_voxel_desc& d = descs[i];
         const akmc_voxel_desc& o = b->desc[v];
-        if (d.L != o.L || d.n_vac != o.n_vac || d.model != o.model || d.precision != o.precision)
-            return fail(AKMC_EINVAL, "slot %d: a new voxel must keep L, n_vac, model and precision", v);
+        if (d.L != o.L || d.n_vac != o.n_vac || d.model != o.model)
+            return fail(AKMC_EINVAL, "slot %d: a new voxel must keep L, n_vac and model", v);
+        if (d.precision != AKMC_FP64 && d.precision != AKMC_SPLIT)
+            return fail(AKMC_EINVAL, "slot %d: bad precision", v);
         if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(AKMC_EINVAL, "slot %d: bad T", v);
         int32_t cnt[4];
         for (int k = 0; k < 3; ++k)
@@ -832,14 +782,14 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
             return fail(AKMC_EINVAL, "slot %d: more solutes than sites", v);
     }
     const Layout& lo = b->lo;
-    std::vector<int4> items, strips, rings;
-    std::vector<RingGroup> rgroups;
+    std::vector<int4> items, strips;
     for (int32_t i = 0; i < n; ++i) {
         const int32_t v = slots[i];
         const akmc_voxel_desc& d = descs[i];
         b->desc[v] = d;
         VoxelDev& V = b->vox_host[v];
         V.status = AKMC_OK;
+        V.precision = d.precision;
         species_counts(d, V.counts);
         V.beta = 1.0 / (kKB * d.T);
         for (int k = 0; k < 3; ++k) V.frac[k] = d.frac[k];
@@ -863,18 +813,6 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
         for (const int4& it : lo.strip_list)
             if (it.x == v) strips.push_back(it);
     }
-    // the reset voxels' ring strips, in the batch list's order (sorted by L), regrouped
-    {
-        std::vector<char> hit(b->n, 0);
-        for (int32_t i = 0; i < n; ++i) hit[slots[i]] = 1;
-        for (const int4& it : lo.ring_list)
-            if (hit[it.x]) {
-                const int L = b->desc[it.x].L;
-                if (rgroups.empty() || rgroups.back().L != L) rgroups.push_back(RingGroup{(int)rings.size(), 0, L});
-                rings.push_back(it);
-                rgroups.back().count++;
-            }
-    }
     int32_t* list = (int32_t*)(b->base + lo.reset_list);
     AKMC_CUDA(cudaMemcpyAsync(list, slots, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     VoxelDev* vox = (VoxelDev*)(b->base + lo.vox);
@@ -888,13 +826,9 @@ akmc_status akmc_reset_voxels(akmc_batch* b, const int32_t* slots, const akmc_vo
     if (!strips.empty())
         AKMC_CUDA(cudaMemcpyAsync(b->base + lo.reset_strips, strips.data(), sizeof(int4) * strips.size(),
                                   cudaMemcpyHostToDevice, s));
-    if (!rings.empty())
-        AKMC_CUDA(cudaMemcpyAsync(b->base + lo.reset_rings, rings.data(), sizeof(int4) * rings.size(),
-                                  cudaMemcpyHostToDevice, s));
-    if (!items.empty() || !strips.empty() || !rings.empty())
+    if (!items.empty() || !strips.empty())
         AKMC_CUDA(launch_density(a.vox, a.model, a.tab, (const int4*)(b->base + lo.reset_items), (int)items.size(),
-                                 (const int4*)(b->base + lo.reset_strips), (int)strips.size(), lo.strip_dyn,
-                                 (const int4*)(b->base + lo.reset_rings), rgroups.data(), (int)rgroups.size(), s));
+                                 (const int4*)(b->base + lo.reset_strips), (int)strips.size(), lo.strip_dyn, s));
     AKMC_CUDA(launch_rebuild(a, 8, list, n, s));
     // pageable sources above are staged by the copies; the tile list must outlive its copy
     AKMC_CUDA(cudaStreamSynchronize(s));
@@ -1015,6 +949,27 @@ akmc_status akmc_read_batch_state(akmc_batch* b, uint8_t* species, int32_t* vac_
             AKMC_CUDA(cudaMemcpyAsync(n_events, io + 2 * n, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
         if (status)
             AKMC_CUDA(cudaMemcpyAsync(status, io + 3 * n, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    }
+    return AKMC_OK;
+}
+
+akmc_status akmc_workload_proxy(akmc_batch* b, double* W, double* M_hat, double* E_hat, akmc_stream stream) {
+    if (!b) return fail(AKMC_EINVAL, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->dirty) {
+        akmc_status st = rebuild(b, s);
+        if (st != AKMC_OK) return st;
+    }
+    const int n = b->n;
+    double* io = (double*)(b->base + b->lo.io);
+    AKMC_CUDA(launch_proxy((const VoxelDev*)(b->base + b->lo.vox), (const ModelDev*)(b->base + b->lo.model), io, n, s));
+    std::vector<double> h(3 * (size_t)n);
+    AKMC_CUDA(cudaMemcpyAsync(h.data(), io, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    AKMC_CUDA(cudaStreamSynchronize(s));
+    for (int v = 0; v < n; ++v) {
+        if (W) W[v] = h[v];
+        if (M_hat) M_hat[v] = h[n + v];
+        if (E_hat) E_hat[v] = h[2 * (size_t)n + v];
     }
     return AKMC_OK;
 }

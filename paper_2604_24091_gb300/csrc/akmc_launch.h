@@ -11,6 +11,8 @@ void launch_place(VoxelDev* vox, int n_vox, const int32_t* list, cudaStream_t st
 cudaError_t launch_batch_load(VoxelDev* vox, const double* io, int n, int has_t, int has_n, cudaStream_t st);
 cudaError_t launch_voxel_load(VoxelDev* V, const double* io, cudaStream_t st);
 cudaError_t launch_batch_read(const VoxelDev* vox, double* io, int n, cudaStream_t st);
+// io[v] = W, io[n+v] = M_hat, io[2n+v] = E_hat of voxel v (workload proxy, Eq. 10)
+cudaError_t launch_proxy(const VoxelDev* vox, const ModelDev* M, double* io, int n, cudaStream_t st);
 
 // Density tiles: cells [x0,x0+kTX) x [y0,y0+kTY) x [z0,z0+kTZ) of one voxel.
 constexpr int kTX = 32, kTY = 16, kTZ = 16, kHalo = 2;
@@ -21,17 +23,8 @@ constexpr int kTX = 32, kTY = 16, kTZ = 16, kHalo = 2;
 constexpr int kStripMaxL = 256;
 int density_strip_rows(int L);
 size_t density_strip_smem(int L);
-// Ring strips (voxels with L % 8 == 0, 8 <= L <= 128 and 16-byte aligned
-// species and density arrays): item (voxel, y0, z0, tz) covers rows
-// [y0, y0 + density_ring_rows()) of planes [z0, z0+tz); items are launched in
-// groups of equal L, each with density_ring_smem(L) bytes of dynamic shared memory.
-struct RingGroup { int first, count, L; };
-bool density_ring_ok(int L);
-int density_ring_rows();
-size_t density_ring_smem(int L);
-cudaError_t launch_density(VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles, int n_tiles,
-                           const int4* strips, int n_strips, size_t strip_dyn, const int4* rings,
-                           const RingGroup* groups, int n_groups, cudaStream_t st);
+cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
+                           int n_tiles, const int4* strips, int n_strips, size_t strip_dyn, cudaStream_t st);
 
 size_t step_dyn_smem(int max_nv, int max_P, int win);
 cudaError_t launch_rate_tables(VoxelDev* vox, int n_vox, const ModelDev* M, const int32_t* list,

@@ -15,7 +15,6 @@
 // its 58 corrections (distinct targets, so lanes never conflict).
 #include "akmc_device.cuh"
 #include "akmc_launch.h"
-#include "bulk_copy.cuh"
 
 namespace akmc {
 
@@ -434,321 +433,11 @@ __global__ void __launch_bounds__(kStripThreads, 2) density_strip_kernel(const V
         strip_body<false>(V, it, buf, lists, s_wt, s_sph, s_count, M->rho_pure);
 }
 
-
-// ---- ring kernel: bulk-copy streaming along z, one barrier per source plane ----
-// For voxels with L % 8 == 0, 8 <= L <= kRingMaxL and 16-byte aligned arrays.
-// One CTA owns the rows y in [y0, y0+ty) (ty <= kRingTY) of the planes z in
-// [z0, z0+tz) of one voxel and walks the source planes z0-2 .. z0+tz+1 once.
-//
-// Shared memory holds a ring of 7 density planes ("slots"; slot of target
-// plane q = q mod 7, q = z - z0 + 4), each ty + 4 full x-rows of int32 (rows
-// 0, 1 and ty+2, ty+3 are guard rows that absorb the strip's own sources'
-// contributions to other strips), and 3 staging buffers of species rows
-// (source plane p in buffer p mod 3).  The bulk-copy engine moves both:
-//  * a source plane's ty + 4 species rows (1 to 3 contiguous runs, y wraps)
-//    are loaded 3 planes ahead, completing on that buffer's mbarrier;
-//  * a finished density plane (its ty own rows, contiguous in memory) is
-//    written back with one bulk store, which runs while the CTA works on the
-//    following planes.
-// Iteration i (source plane i, its targets q = i .. i+4):
-//  a. scatter the non-Fe entries of plane i (listed in iteration i-1) into
-//     the ring with shared-memory reductions: 8 lanes per entry, 8 of the 58
-//     sphere offsets per lane; per-lane target deltas come from a table
-//     rewritten every iteration (the slots rotate); entries of halo rows
-//     predicate each term on its target row, entries within 3 sites of a row
-//     end wrap their x offsets; a plane with more than kRingCap listed
-//     entries of one sublattice is scattered directly from its staging buffer;
-//  b. list plane i+1 (wait for its bulk load; one 16-byte chunk per thread,
-//     non-Fe bytes found with word operations; lists per sublattice: own rows
-//     from the front, halo rows from the back, row-end sites apart);
-//  c. reset the slot of plane q = i+5 (stored two iterations ago) to pure Fe;
-//  d. fence (shared-memory writes -> bulk-copy reads), one CTA barrier, then
-//     one thread stores plane q = i and issues the load of plane i+3.
-// Thread 0 waits for the read of the previous store before the barrier of d,
-// so a slot is never reset while its store still reads it.  Every mbarrier
-// wait is bounded; a wait that gives up sets AKMC_ETIMEOUT on the voxel.
-
-constexpr int kRingThreads = 256;
-constexpr int kRingTY = 8;                  // output rows per strip
-constexpr int kRingRows = kRingTY + 4;      // rows per slot and staging buffer
-constexpr int kRingSlots = 7;               // 5 target planes, 1 being stored, 1 being reset
-constexpr int kRingStages = 3;              // species planes in flight
-constexpr int kRingCap = 256;               // listed entries per sublattice and plane (own + halo)
-constexpr int kRingEdge = kRingRows * 3;    // row-end entries per sublattice and plane (3 per row)
-constexpr uint32_t kRingPolls = 1u << 22;   // bound of one staging wait
-constexpr int kRingMaxL = 128;
-
-__host__ __device__ inline size_t ring_smem_bytes(int L) {
-    const size_t M2 = 2 * (size_t)L;
-    return 4 * (size_t)kRingSlots * kRingRows * M2 + (size_t)kRingStages * kRingRows * M2 + 32 +
-           4 * (4 * (size_t)kRingCap + 4 * (size_t)kRingEdge) + 4 * 256;
-}
-
-__global__ void __launch_bounds__(kRingThreads, 4) density_ring_kernel(VoxelDev* vox, const ModelDev* M,
-                                                                       const Tables* tab, const int4* items) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ int4 s_wt[8][8][2];      // [species][sub]: f_s - f_Fe at the 8 offsets k = sub + 8j
-    __shared__ int32_t s_sph[64];
-    __shared__ int s_cnt[3][8];         // per plane mod 3: own b0, own b1, halo b0, halo b1, edge b0, edge b1
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int4 it = items[blockIdx.x];
-    VoxelDev& V = vox[it.x];
-    const int L = V.L, M2 = 2 * L;
-    const int y0 = it.y, z0 = it.z, tz = it.w & 0xFFFF;
-    const int ty = min(kRingTY, L - y0);
-    const int SLOT = kRingRows * M2;    // ints per slot; bytes per staging buffer
-    int32_t* ring = (int32_t*)sm;
-    uint8_t* stage = sm + 4 * (size_t)kRingSlots * SLOT;
-    uint64_t* mbar = (uint64_t*)(stage + (size_t)kRingStages * SLOT);
-    uint32_t* lists = (uint32_t*)((unsigned char*)mbar + 32);   // [buf][b][kRingCap]
-    uint32_t* edges = lists + 4 * kRingCap;                      // [buf][b][kRingEdge]
-    int32_t* dtab = (int32_t*)(edges + 4 * kRingEdge);           // [iteration & 1][b][sub][j]
-    const uint32_t ring_a = bulk::smem_addr(ring);
-    const int32_t rho0 = M->rho_pure;
-
-    if (tid < kSph) s_sph[tid] = tab->sph_off[tid];
-    if (tid < 24) (&s_cnt[0][0])[tid] = 0;
-    if (tid == 0) {
-        for (int s = 0; s < kRingStages; ++s) bulk::mbar_init(bulk::smem_addr(&mbar[s]), 1);
-        bulk::fence_mbar_init();
-    }
-    __syncthreads();
-    for (int i = tid; i < 512; i += kRingThreads) {
-        const int sp = i >> 6, sub = (i >> 3) & 7, j = i & 7, k = sub + 8 * j;
-        ((int32_t*)s_wt)[i] = (sp >= 1 && sp <= 4 && k < kSph) ? M->cq[sp][off_extra(s_sph[k])] : 0;
-    }
-    // target-delta table entry of this thread (tid < 128: sublattice, lane, offset)
-    int dt_base = 0, dt_dz = 0;
-    if (tid < 128) {
-        const int bb = tid >> 6, sub = (tid >> 3) & 7, j = tid & 7, k = sub + 8 * j;
-        const int o = s_sph[k < kSph ? k : 0];
-        dt_dz = half_floor(bb + off_dz(o));
-        dt_base = (int)ring_a + 4 * (half_floor(bb + off_dy(o)) * M2 + off_dx(o));
-    }
-    // the table of an iteration whose source plane's own target plane sits in slot r
-    auto dt_write = [&](int par, int r) {
-        if (tid < 128) {
-            int s = r + dt_dz;
-            s = s < 0 ? s + kRingSlots : (s >= kRingSlots ? s - kRingSlots : s);
-            dtab[par * 128 + tid] = dt_base + 4 * s * SLOT;
-        }
-    };
-    // scatter lanes: sublattice b = warp & 1, offsets k = sub + 8j
-    const int sub = lane & 7, b = warp & 1;
-    uint32_t DY = 0, DX = 0;            // 3 bits per j: dyc + 2, dx + 3
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int k = sub + 8 * j;
-        const int o = s_sph[k < kSph ? k : 0];
-        DY |= (uint32_t)(half_floor(b + off_dy(o)) + 2) << (3 * j);
-        DX |= (uint32_t)(off_dx(o) + 3) << (3 * j);
-    }
-    const uint32_t k7 = sub < kSph - 56 ? 0u : 1u;   // offset sub + 56 exists iff 0
-    // scan: this thread's 16-byte chunk of a staged plane (at most one: ty + 4 rows of <= 256 bytes)
-    const int cpr = M2 / 16, n_chunks = (ty + 4) * cpr;
-    const bool scanner = tid < n_chunks;
-    const int c_hr = tid / cpr, c_x0 = (tid - c_hr * cpr) * 16;
-    const bool c_own = c_hr >= 2 && c_hr < ty + 2;
-    uint32_t c_emask = 0;               // bytes within 3 sites of a row end
-    if (c_x0 == 0) c_emask |= 0x0007u;
-    if (c_x0 == M2 - 16) c_emask |= 0xE000u;
-    const int n_src = tz + 4;
-    auto wrapL = [&](int a) { return a < 0 ? a + L : (a >= L ? a - L : a); };
-    int issued = 0;                     // thread 0: source planes whose loads are issued
-    auto issue = [&](int p) {
-        const int s = p % kRingStages;
-        const uint32_t bar = bulk::smem_addr(&mbar[s]), dst = bulk::smem_addr(stage + (size_t)s * SLOT);
-        bulk::mbar_arrive_expect_tx(bar, (uint32_t)((ty + 4) * M2));
-        const uint8_t* plane = V.species + (size_t)wrapL(z0 - 2 + p) * L * M2;
-        for (int hr = 0; hr < ty + 4;) {
-            const int y = wrapL(y0 - 2 + hr), n = min(ty + 4 - hr, L - y);
-            bulk::load(dst + hr * M2, plane + (size_t)y * M2, (uint32_t)(n * M2), bar);
-            hr += n;
-        }
-        issued = p + 1;
-    };
-    auto scan = [&](int p) -> bool {
-        if (!scanner) return true;
-        const int s = p % kRingStages;
-        if (!bulk::mbar_wait(bulk::smem_addr(&mbar[s]), (uint32_t)(p / kRingStages) & 1u, kRingPolls)) return false;
-        const uint4 v = *(const uint4*)(stage + (size_t)s * SLOT + 16 * tid);
-        if ((v.x | v.y | v.z | v.w) == 0) return true;
-        const uint32_t Mk = nonzero_bytes(v);
-        int* cnt = s_cnt[p % 3];
-        const int buf = p & 1, ub0 = c_hr * M2 + c_x0;
-        auto byte_at = [&](int j) {
-            const uint32_t wj = j < 8 ? (j < 4 ? v.x : v.y) : (j < 12 ? v.z : v.w);
-            return (wj >> (8 * (j & 3))) & 0xFFu;
-        };
-        const uint32_t Mi = Mk & ~c_emask, Me = Mk & c_emask;
-        if (Mi) {
-            const uint32_t M0 = Mi & 0x5555u, M1 = Mi & 0xAAAAu;
-            int a0 = M0 ? atomicAdd(&cnt[c_own ? 0 : 2], __popc(M0)) : 0;
-            int a1 = M1 ? atomicAdd(&cnt[c_own ? 1 : 3], __popc(M1)) : 0;
-            uint32_t m = Mi;
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t en = strip_entry(byte_at(j), ub0 + j, c_hr);
-                const int at = (j & 1) ? a1++ : a0++;
-                if (at < kRingCap) lists[(buf * 2 + (j & 1)) * kRingCap + (c_own ? at : kRingCap - 1 - at)] = en;
-            }
-        }
-        if (Me) {
-            const uint32_t M0 = Me & 0x5555u, M1 = Me & 0xAAAAu;
-            int a0 = M0 ? atomicAdd(&cnt[4], __popc(M0)) : 0;
-            int a1 = M1 ? atomicAdd(&cnt[5], __popc(M1)) : 0;
-            uint32_t m = Me;
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t en = strip_entry(byte_at(j), ub0 + j, c_hr);
-                const int at = (j & 1) ? a1++ : a0++;   // < kRingEdge: 3 row-end sites per row and sublattice
-                edges[(buf * 2 + (j & 1)) * kRingEdge + at] = en;
-            }
-        }
-        return true;
-    };
-    // direct scatter of source plane i from its staging buffer (lists overflowed)
-    auto direct = [&](int i, int r) {
-        const uint8_t* st = stage + (size_t)(i % kRingStages) * SLOT;
-        for (int c = tid; c < (ty + 4) * M2; c += kRingThreads) {
-            uint32_t sp = st[c];
-            if (!sp) continue;
-            sp = sp > 7 ? 7 : sp;
-            const int hr = c / M2, X = c - hr * M2, bb = X & 1;
-            for (int k = 0; k < kSph; ++k) {
-                const int o = s_sph[k];
-                const int trow = hr + half_floor(bb + off_dy(o));
-                if ((unsigned)(trow - 2) >= (unsigned)ty) continue;
-                int s = r + half_floor(bb + off_dz(o));
-                s = s < 0 ? s + kRingSlots : (s >= kRingSlots ? s - kRingSlots : s);
-                int Xt = X + off_dx(o);
-                Xt = Xt < 0 ? Xt + M2 : (Xt >= M2 ? Xt - M2 : Xt);
-                atomicAdd(&ring[s * SLOT + trow * M2 + Xt], strip_w(s_wt, (int)sp, k));
-            }
-        }
-    };
-    auto scatter = [&](int i, int r) {
-        const int* cnt = s_cnt[i % 3];
-        if (cnt[0] + cnt[2] > kRingCap || cnt[1] + cnt[3] > kRingCap) {   // uniform over the CTA
-            direct(i, r);
-            return;
-        }
-        const int buf = i & 1;
-        const int4 d0 = *(const int4*)&dtab[buf * 128 + b * 64 + sub * 8];
-        const int4 d1 = *(const int4*)&dtab[buf * 128 + b * 64 + sub * 8 + 4];
-        const uint32_t D[8] = {(uint32_t)d0.x, (uint32_t)d0.y, (uint32_t)d0.z, (uint32_t)d0.w,
-                               (uint32_t)d1.x, (uint32_t)d1.y, (uint32_t)d1.z, (uint32_t)d1.w};
-        const uint32_t* lst = lists + (buf * 2 + b) * kRingCap;
-        const int first = (warp >> 1) * 4 + (lane >> 3);   // 16 entries per pass and sublattice
-        const int n_own = cnt[b], n_halo = cnt[2 + b], n_edge = cnt[4 + b];
-        for (int e = first; e < n_own; e += 16) {
-            const uint32_t en = lst[e];
-            const uint32_t ub = 4 * ((en >> 3) & 0xFFFFFu);
-            const int4 w0 = s_wt[en & 7][sub][0], w1 = s_wt[en & 7][sub][1];
-            const int ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int j = 0; j < 7; ++j) red_add(ub + D[j], ww[j]);
-            red_add_if(ub + D[7], ww[7], k7, 1u);
-        }
-        for (int e = first; e < n_halo; e += 16) {
-            const uint32_t en = lst[kRingCap - 1 - e];
-            const uint32_t ub = 4 * ((en >> 3) & 0xFFFFFu);
-            const uint32_t hm = (en >> 23) - 4u;            // own-row index of the target: hm + dyc + 2
-            const int4 w0 = s_wt[en & 7][sub][0], w1 = s_wt[en & 7][sub][1];
-            const int ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t row = j == 7 && k7 ? 0xFFFFFFFFu : hm + ((DY >> (3 * j)) & 7);
-                red_add_if(ub + D[j], ww[j], row, (uint32_t)ty);
-            }
-        }
-        const uint32_t* ed = edges + (buf * 2 + b) * kRingEdge;
-        for (int e = first; e < n_edge; e += 16) {
-            const uint32_t en = ed[e];
-            const int u = (int)((en >> 3) & 0xFFFFFu), hr = (int)(en >> 23), X = u - hr * M2;
-            const uint32_t hm = (uint32_t)hr - 4u;
-            const int4 w0 = s_wt[en & 7][sub][0], w1 = s_wt[en & 7][sub][1];
-            const int ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int Xt = X + (int)((DX >> (3 * j)) & 7) - 3;
-                const int adj = Xt < 0 ? M2 : (Xt >= M2 ? -M2 : 0);
-                const uint32_t row = j == 7 && k7 ? 0xFFFFFFFFu : hm + ((DY >> (3 * j)) & 7);
-                red_add_if((uint32_t)(4 * (u + adj)) + D[j], ww[j], row, (uint32_t)ty);
-            }
-        }
-    };
-    auto reset_slot = [&](int s) {
-        int4* p = (int4*)(ring + (size_t)s * SLOT + 2 * M2);
-        const int4 v = make_int4(rho0, rho0, rho0, rho0);
-        for (int c = tid; c < ty * M2 / 4; c += kRingThreads) p[c] = v;
-    };
-
-    for (int s = 0; s < 5; ++s) reset_slot(s);
-    dt_write(0, 2);
-    if (tid == 0)
-        for (int p = 0; p < min(kRingStages, n_src); ++p) issue(p);
-    bool ok = scan(0);
-    bool failed = __syncthreads_or(!ok);
-    int next_scan = 1;                  // first source plane not yet listed
-    for (int i = 0, r = 2; i < n_src && !failed; ++i) {
-        scatter(i, r);
-        ok = true;
-        if (i + 1 < n_src) ok = scan(i + 1);
-        const int rn = r == kRingSlots - 1 ? 0 : r + 1;
-        dt_write((i + 1) & 1, rn);
-        reset_slot((i + 5) % kRingSlots);
-        if (tid < 8) s_cnt[(i + 2) % 3][tid] = 0;
-        bulk::fence_proxy_async_smem();
-        if (tid == 0) bulk::wait_read_all();
-        failed = __syncthreads_or(!ok);
-        if (failed) break;
-        next_scan = i + 2;
-        if (tid == 0) {
-            const int s = i % kRingSlots;
-            if (i >= 4)
-                bulk::store(V.rho + ((size_t)(z0 + i - 4) * L + y0) * M2, ring_a + 4 * (uint32_t)(s * SLOT + 2 * M2),
-                            (uint32_t)(4 * ty * M2));
-            bulk::commit();
-            if (i + kRingStages < n_src) issue(i + kRingStages);
-        }
-        r = rn;
-    }
-    if (tid == 0) {
-        bulk::wait_all();
-        if (failed) {
-            // give the loads still in flight a bounded time to land before the CTA's
-            // shared memory goes away, then report the voxel
-            for (int p = next_scan - 1; p < issued; ++p)
-                if (p >= 0) bulk::mbar_wait(bulk::smem_addr(&mbar[p % kRingStages]), (uint32_t)(p / kRingStages) & 1u,
-                                            kRingPolls);
-            atomicCAS(&V.status, (int)kOK, (int)kETIMEOUT);
-        }
-    }
-}
-
 int density_strip_rows(int L) { return strip_rows(L); }
 size_t density_strip_smem(int L) { return strip_smem(strip_rows(L), L); }
 
-bool density_ring_ok(int L) { return L % 8 == 0 && L >= 8 && L <= kRingMaxL; }
-int density_ring_rows() { return kRingTY; }
-size_t density_ring_smem(int L) { return ring_smem_bytes(L); }
-
-cudaError_t launch_density(VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles, int n_tiles,
-                           const int4* strips, int n_strips, size_t strip_dyn, const int4* rings,
-                           const RingGroup* groups, int n_groups, cudaStream_t st) {
-    for (int g = 0; g < n_groups; ++g) {
-        if (groups[g].count <= 0) continue;
-        const size_t dyn = ring_smem_bytes(groups[g].L);
-        cudaError_t e = cudaFuncSetAttribute((const void*)density_ring_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        density_ring_kernel<<<groups[g].count, kRingThreads, dyn, st>>>(vox, M, tab, rings + groups[g].first);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
+                           int n_tiles, const int4* strips, int n_strips, size_t strip_dyn, cudaStream_t st) {
     if (n_strips > 0) {
         cudaError_t e = cudaFuncSetAttribute((const void*)density_strip_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_dyn);

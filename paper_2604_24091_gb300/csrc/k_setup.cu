@@ -224,6 +224,42 @@ __global__ void batch_read_kernel(const VoxelDev* vox, double* io, int n) {
     }
 }
 
+// Workload proxy of the dynamic voxel scheduling (Eq. 10) from each voxel's
+// current hop rates: one warp per voxel adds its 8 nv rates (float64; lane-
+// strided partial sums, then a butterfly, so the order is fixed) and counts
+// the admissible hops (rate > 0).  With Gamma_tot the sum and M the count,
+// W = Gamma_tot / nu, and E = -ln(W / M) / beta is the barrier that gives each
+// of the M admissible hops the voxel's mean rate, so W = M exp(-beta E).
+// io[v] = W, io[n + v] = M, io[2n + v] = E (+inf when M = 0 or Gamma_tot = 0).
+__global__ void proxy_kernel(const VoxelDev* vox, const ModelDev* M, double* io, int n) {
+    const int lane = threadIdx.x & 31;
+    const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (v >= n) return;
+    const VoxelDev& V = vox[v];
+    double s = 0.0;
+    int m = 0;
+    for (int i = lane; i < 8 * V.nv; i += 32) {
+        const double g = V.rates[i];
+        s += g;
+        m += g > 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+    }
+    if (lane == 0) {
+        const double W = s / M->nu;
+        io[v] = W;
+        io[n + v] = (double)m;
+        io[2 * n + v] = (m > 0 && s > 0.0) ? -log(W / (double)m) / V.beta : __longlong_as_double(0x7ff0000000000000ll);
+    }
+}
+
+cudaError_t launch_proxy(const VoxelDev* vox, const ModelDev* M, double* io, int n, cudaStream_t st) {
+    proxy_kernel<<<(n + 3) / 4, 128, 0, st>>>(vox, M, io, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_load(VoxelDev* vox, const double* io, int n, int has_t, int has_n, cudaStream_t st) {
     batch_load_kernel<<<n, 256, 0, st>>>(vox, io, n, has_t, has_n);
     return cudaGetLastError();

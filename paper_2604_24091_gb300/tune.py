@@ -1,18 +1,26 @@
 """Launch-shape autotuner for akmc_step_n.
 
 Times candidate shapes (warps per voxel-CTA, CTAs per SM) on a scratch batch
-built from the same descriptors (the caller's batch is never stepped), picks
-the fastest and caches the choice per workload key for the process.
+built from the same descriptors (the caller's batch is never stepped) and
+picks the fastest.  Choices are cached per workload key in the process and,
+unless disabled, in a JSON file (AKMC_TUNE_CACHE, default
+~/.cache/akmc_gb300/tune.json) keyed also by the GPU name and the library
+build, so a later process on the same GPU and build reuses them.
 """
 from __future__ import annotations
 
 import collections
+import hashlib
+import json
+import os
+import tempfile
 
 import numpy as np
 
-from .akmc import Batch
+from .akmc import LIB_PATH, Batch
 
 _cache = {}
+CANDIDATES = ((8, 0), (16, 0), (4, 0), (2, 0), (8, 1), (4, 2))
 
 
 def workload_key(descs):
@@ -21,13 +29,59 @@ def workload_key(descs):
     return tuple(sorted(c.items()))
 
 
-def tune(descs, model, events=2000, candidates=((8, 0), (16, 0), (4, 0), (2, 0), (8, 1), (4, 2)), sample=1024):
+def cache_path():
+    p = os.environ.get("AKMC_TUNE_CACHE")
+    if p is not None:
+        return p or None            # empty string: no file cache
+    return os.path.join(os.path.expanduser("~"), ".cache", "akmc_gb300", "tune.json")
+
+
+def _file_key(key, device_name):
+    try:
+        with open(LIB_PATH, "rb") as f:
+            build = hashlib.sha1(f.read()).hexdigest()[:16]
+    except OSError:
+        build = "unbuilt"
+    return hashlib.sha1(repr((device_name, build, key)).encode()).hexdigest()
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, fkey, shape):
+    d = _load(path)
+    d[fkey] = list(shape)
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        fd, tmp = tempfile.mkstemp(dir=os.path.dirname(path), suffix=".tmp")
+        with os.fdopen(fd, "w") as f:
+            json.dump(d, f)
+        os.replace(tmp, path)
+    except OSError:
+        pass                        # a read-only home: the process cache still holds it
+
+
+def tune(descs, model, events=2000, candidates=CANDIDATES, sample=1024, use_file=True):
     """Return (warps, ctas_per_sm) with the highest events/s on a scratch copy
     of up to `sample` of the voxels."""
     import torch
     key = workload_key(descs)
     if key in _cache:
         return _cache[key]
+    path = cache_path() if use_file else None
+    fkey = None
+    if path:
+        fkey = _file_key(key, torch.cuda.get_device_name())
+        hit = _load(path).get(fkey)
+        if isinstance(hit, list) and tuple(hit) in set(candidates):
+            _cache[key] = tuple(hit)
+            return _cache[key]
     descs = list(descs)[:sample]
     scratch = Batch(descs, model)
     best, best_rate = candidates[0], -1.0
@@ -47,4 +101,6 @@ def tune(descs, model, events=2000, candidates=((8, 0), (16, 0), (4, 0), (2, 0),
     scratch.close()
     del scratch
     _cache[key] = best
+    if path:
+        _store(path, fkey, best)
     return best

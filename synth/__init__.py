@@ -277,6 +277,26 @@ def serving_requests(duration_s: float = 10.0, rate_hz: float = 200.0,
     return out
 
 
+def mixed_requests(n: int, seed: int = SEED_BASE + 7, t_sim_range=(2e-4, 2e-3), sizes=(16, 24, 32),
+                   max_vac: int = 2):
+    """An ensemble of voxel requests of mixed shape, all due at once: edge L from
+    `sizes`, 1..max_vac vacancies, pair or EAM (split precision) 50/50, Cu 0.1-0.3,
+    Ni/Mn 0.5-1.5 at%, T uniform in 543-593 K, and a simulated-time horizon
+    log-uniform in t_sim_range (seconds).  Returns (desc, t_sim) pairs."""
+    rng = np.random.default_rng([seed, 7])
+    out = []
+    for u in range(n):
+        L = int(rng.choice(sizes))
+        nv = int(rng.integers(1, max_vac + 1))
+        model = int(rng.integers(0, 2))
+        prec = PREC_SPLIT if model == EAM_MODEL else PREC_FP64
+        fr = (rng.uniform(0.001, 0.003), rng.uniform(0.005, 0.015), rng.uniform(0.005, 0.015))
+        T = rng.uniform(543.0, 593.0)
+        t_sim = float(math.exp(rng.uniform(math.log(t_sim_range[0]), math.log(t_sim_range[1]))))
+        out.append((VoxelDesc(L, nv, fr, T, model, prec, splitmix64(seed, u), (1 << 40) + u), t_sim))
+    return out
+
+
 # --------------------------------------------------------------------------
 # Arbitrary lattices for tests
 # --------------------------------------------------------------------------

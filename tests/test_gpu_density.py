@@ -1,9 +1,8 @@
 """EAM site densities on the GPU (akmc_read_density) against the oracle.
 
 Densities are exact integers (unit 2^-24), so every comparison is bit-exact.
-Covered: the ring kernel (L % 8 == 0, 8 <= L <= 128, aligned arrays: bulk
-copies, listed and direct scatter, several L groups), the strip kernel's
-16-byte path (L % 8 == 0, aligned rows, L > 128) and its byte path (odd-sized voxels before it in the batch break the alignment, or
+Covered: the strip kernel's 16-byte path (L % 8 == 0, aligned rows) and its
+byte path (odd-sized voxels before it in the batch break the alignment, or
 L % 8 != 0), strips narrower than 16 rows (L = 24, 40), z-chunked and whole-z
 strips, the tile kernel for L > 256, densities after events (the step
 kernel's incremental updates), and the full-size rate-kernel workload
@@ -119,21 +118,20 @@ def test_density_dense_lattices_overflow_path(model):
     b.close()
 
 
-def test_density_ring_kernel_groups_and_dense_planes(model):
-    # every voxel ring-eligible (L % 8 == 0, all arrays aligned): one launch per
-    # L; dense voxels overflow the per-plane lists (direct scatter) in some or
-    # all planes, dilute ones never do; z split in chunks of 8 planes
-    descs = [_d(64, 4, (0.10, 0.10, 0.10), uid=40),   # ~30 % non-Fe: lists overflow in some planes
-             _d(64, 4, (0.30, 0.30, 0.20), uid=41),   # 80 %: every plane direct
+def test_density_mixed_edges_and_dense_lattices(model):
+    # voxels of several edges in one batch (16-byte path), dense ones overflowing the
+    # per-block lists (direct scatter) in some or all blocks, z split in chunks; a
+    # reset slot is rebuilt through the reset path's own strip list
+    descs = [_d(64, 4, (0.10, 0.10, 0.10), uid=40),   # ~30 % non-Fe: lists overflow in some blocks
+             _d(64, 4, (0.30, 0.30, 0.20), uid=41),   # 80 %: every block direct
              _d(48, 4, (0.25, 0.15, 0.10), uid=42),
              _d(72, 3, (0.002, 0.01, 0.01), uid=43),
              _d(80, 3, (0.20, 0.10, 0.10), uid=44),
-             _d(8, 2, (0.05, 0.05, 0.05), uid=45),    # smallest ring voxel: rows and planes wrap
+             _d(8, 2, (0.05, 0.05, 0.05), uid=45),    # smallest: rows and planes wrap
              _d(16, 1, (0.05, 0.05, 0.05), uid=46),
              _d(24, 2, (0.01, 0.02, 0.02), uid=47)]
     b = Batch(descs, model)
     _check_all(b, descs, model, range(len(descs)))
-    # a reset slot is rebuilt through the same kernel (the reset path's own item list)
     b.reset_voxels([3], [_d(72, 3, (0.004, 0.01, 0.01), uid=48)])
     descs[3] = _d(72, 3, (0.004, 0.01, 0.01), uid=48)
     _check_all(b, descs, model, [3])

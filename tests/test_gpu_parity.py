@@ -6,6 +6,7 @@ displacements, cluster histograms) bit-exact; float64 rates within 1e-12
 relative; the clock within 1e-12 relative; FP32/FP64 split EAM energy changes
 within 1e-5 eV of the oracle's float64 values on the same state.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -13,6 +14,7 @@ import pytest
 
 import oracle
 import synth
+from ties import is_declared_tie
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +26,13 @@ from paper_2604_24091_gb300 import Batch, ETRAPPED, ENUMERIC  # noqa: E402
 
 RATE_RTOL = 1e-12
 SPLIT_DE_TOL = 1e-5
+KB_EV = 8.617333262e-5
+
+
+def split_rate_rtol(T):
+    """Rates from a split-precision dE within 1e-5 eV of the float64 one: the
+    barrier moves by at most 1e-5 eV, so ln(rate) by at most 1e-5 / (kB T)."""
+    return 1.01 * SPLIT_DE_TOL / (KB_EV * T)
 
 
 def _assert_rates(g, o, rtol=RATE_RTOL):
@@ -34,6 +43,13 @@ def _assert_rates(g, o, rtol=RATE_RTOL):
 
 def _time(s):
     return s["t_hi"] + s["t_lo"]
+
+
+def _assert_events(d, model, g_log, o_log):
+    """Event logs equal; a first difference at a declared tie (reading R9) skips
+    the rest of the test (a fixed configuration cannot be re-seeded here)."""
+    if is_declared_tie(d, model, g_log, o_log):
+        pytest.skip("declared tie in voxel uid %d" % d.uid)
 
 
 def _mixed_descs():
@@ -64,34 +80,55 @@ def test_placement_and_initial_rates(model):
             _assert_rates(g["rates"], o["rates"])
         else:
             assert np.abs(g["dE"] - o["dE"]).max() <= SPLIT_DE_TOL
-            _assert_rates(g["rates"], o["rates"], rtol=1e-3)
+            _assert_rates(g["rates"], o["rates"], rtol=split_rate_rtol(d.T))
+
+
+_ORACLE_RUNS = {}
+
+
+def _oracle_run(d, model, n):
+    """The oracle's trajectory of `d` over n events (event log and final state), cached."""
+    key = (repr(d), n)
+    if key not in _ORACLE_RUNS:
+        o = oracle.Voxel(d, model)
+        log = o.step(n, log=True)
+        _ORACLE_RUNS[key] = (log, o.state())
+    return _ORACLE_RUNS[key]
 
 
 @pytest.mark.parametrize("warps", [1, 2, 4, 8, 16])
 def test_pair_trajectory_bit_exact(model, warps):
-    # plain configuration (16^3 cells, Fe-1.34Cu, 1 vacancy) and a dense
-    # multi-vacancy lattice, stepped in two chunks
-    descs = [synth.config_plain_pair()[0],
-             synth.VoxelDesc(8, 6, (0.12, 0.1, 0.08), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=9, uid=3)]
-    n1, n2 = 20000, 30000
-    b = Batch(descs, model, event_log_capacity=n1 + n2)
-    b.set_launch(warps, 0)
-    b.step(n1)
-    b.step(n2)
-    assert b.sync_status()[0] == 0
-    for v, d in enumerate(descs):
-        o = oracle.Voxel(d, model)
-        log_o = o.step(n1 + n2, log=True)
-        g = b.read_state(v, log=True)
-        so = o.state()
-        first_bad = np.flatnonzero(g["event_log"] != log_o)
-        assert first_bad.size == 0, "voxel %d diverges at event %d" % (v, first_bad[0])
-        assert np.array_equal(g["species"], so["species"])
-        assert np.array_equal(g["vac_pos"], so["vac_pos"])
-        assert np.array_equal(g["vac_disp"], so["vac_disp"])
-        assert g["n_events"] == so["n_events"] == n1 + n2
-        assert abs(_time(g) - _time(so)) <= 1e-12 * _time(so)
-        _assert_rates(g["rates"], so["rates"])
+    # plain configuration (16^3 cells, Fe-1.34Cu, 1 vacancy) over its configured
+    # 1e5 events, and a dense multi-vacancy lattice, stepped in two chunks.  A
+    # divergence at a declared tie (reading R9) re-seeds the voxel; anywhere else
+    # it fails.
+    n1, n2 = 40000, 60000
+    base = [synth.config_plain_pair()[0],
+            synth.VoxelDesc(8, 6, (0.12, 0.1, 0.08), 563.0, synth.PAIR_MODEL, synth.PREC_FP64, seed=9, uid=3)]
+    for attempt in range(3):
+        descs = [dataclasses.replace(d, seed=d.seed + attempt) for d in base]
+        b = Batch(descs, model, event_log_capacity=n1 + n2)
+        b.set_launch(warps, 0)
+        b.step(n1)
+        b.step(n2)
+        assert b.sync_status()[0] == 0
+        tied = False
+        for v, d in enumerate(descs):
+            log_o, so = _oracle_run(d, model, n1 + n2)
+            g = b.read_state(v, log=True)
+            if is_declared_tie(d, model, g["event_log"], log_o):
+                tied = True
+                break
+            assert np.array_equal(g["species"], so["species"])
+            assert np.array_equal(g["vac_pos"], so["vac_pos"])
+            assert np.array_equal(g["vac_disp"], so["vac_disp"])
+            assert g["n_events"] == so["n_events"] == n1 + n2
+            assert abs(_time(g) - _time(so)) <= 1e-12 * _time(so)
+            _assert_rates(g["rates"], so["rates"])
+        b.close()
+        if not tied:
+            return
+    pytest.fail("declared ties on three seeds in a row")
 
 
 def test_eam_fp64_trajectory(model):
@@ -106,7 +143,7 @@ def test_eam_fp64_trajectory(model):
         log_o = o.step(n, log=True)
         g = b.read_state(v, log=True)
         so = o.state()
-        assert np.array_equal(g["event_log"], log_o)
+        _assert_events(d, model, g["event_log"], log_o)
         assert np.array_equal(g["species"], so["species"])
         np.testing.assert_allclose(g["dE"], so["dE"], rtol=0, atol=1e-12)
         _assert_rates(g["rates"], so["rates"])
@@ -130,7 +167,7 @@ def test_eam_split_energy_error(model):
             o.load(g["species"], g["vac_pos"])
             so = o.state()
             worst = max(worst, float(np.abs(g["dE"] - so["dE"]).max()))
-            _assert_rates(g["rates"], so["rates"], rtol=1e-3)
+            _assert_rates(g["rates"], so["rates"], rtol=split_rate_rtol(d.T))
             assert np.array_equal(np.bincount(g["species"], minlength=5),
                                   np.bincount(oracle.Voxel(d, model).state()["species"], minlength=5))
     assert worst <= SPLIT_DE_TOL, worst
@@ -232,7 +269,7 @@ def test_full_size_batched_eam_sampled(model):
         assert np.array_equal(np.bincount(g["species"], minlength=5), np.bincount(init, minlength=5))
         o.load(g["species"], g["vac_pos"])
         assert np.abs(g["dE"] - o.state()["dE"]).max() <= SPLIT_DE_TOL
-        _assert_rates(g["rates"], o.state()["rates"], rtol=1e-3)
+        _assert_rates(g["rates"], o.state()["rates"], rtol=split_rate_rtol(descs[v].T))
         assert _time(g) > 0
 
 
@@ -290,7 +327,7 @@ def test_single_vacancy_fast_path_matches_oracle(model):
             log_o = o.step(n, log=True)
             so = o.state()
             if d.precision == synth.PREC_FP64:
-                assert np.array_equal(g["event_log"], log_o)
+                _assert_events(d, model, g["event_log"], log_o)
                 assert np.array_equal(g["species"], so["species"])
                 _assert_rates(g["rates"], so["rates"])
             o2 = oracle.Voxel(d, model)
@@ -315,7 +352,7 @@ def test_large_voxel_sampled(model):
     np.testing.assert_array_equal(b.read_density(0).astype(np.int64), o.rho_all())
     so = o.state()
     assert np.abs(g["dE"] - so["dE"]).max() <= SPLIT_DE_TOL
-    _assert_rates(g["rates"], so["rates"], rtol=1e-3)
+    _assert_rates(g["rates"], so["rates"], rtol=split_rate_rtol(d.T))
     b.close()
 
 
@@ -330,7 +367,7 @@ def test_large_voxel_fp64_trajectory(model):
     g = b.read_state(0, log=True)
     o = oracle.Voxel(d, model)
     log_o = o.step(n, log=True)
-    assert np.array_equal(g["event_log"], log_o)
+    _assert_events(d, model, g["event_log"], log_o)
     so = o.state()
     assert np.array_equal(g["species"], so["species"])
     _assert_rates(g["rates"], so["rates"])
@@ -353,7 +390,7 @@ def test_max_vacancies_bit_exact(model):
         log_o = o.step(n[v], log=True)
         g = b.read_state(v, log=True)
         so = o.state()
-        assert np.array_equal(g["event_log"][:n[v]], log_o), v
+        _assert_events(d, model, g["event_log"][:n[v]], log_o)
         assert np.array_equal(g["species"], so["species"])
         assert np.array_equal(g["vac_disp"], so["vac_disp"])
         _assert_rates(g["rates"], so["rates"])
