@@ -92,6 +92,7 @@ struct __align__(16) StepShared {
     int32_t pA, pw, pm, pwb, pmb;     // hop whose density change is pending: atom, window sites, parities
     int32_t pwX, pwY, pwZ, pmX, pmY, pmZ;
     double nx1, nx2;                  // uniforms of the event after the next one
+    uint64_t nuU1, nxU1;              // u1 of the next / following event as a 53-bit integer (u1 = U1 2^-53)
     // sublattice superstep (see sl_kernel): counter words of the uniforms,
     // octant bounds (cells) and the octant's clock and window
     int32_t sl_on, sl_k, sl_sid, sl_n, sl_nvtot, sl_etab;
@@ -356,6 +357,51 @@ __device__ __forceinline__ bool finite_bits(double g) {
     return ((__double_as_longlong(g) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// A non-negative float64 x as an unsigned fixed-point mantissa M in
+// [2^63, 2^64) and a binary exponent E, x = M 2^E (M = 0 for zero and
+// subnormal x).
+__device__ __forceinline__ void rate_to_fixed(double x, unsigned long long& M, int& E) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int be = (int)((b >> 52) & 0x7ff);
+    M = be == 0 ? 0ull : (((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11);
+    E = be - 1075 - 11;
+}
+
+// (a4) hop_rate_grid's rate as M 2^E with M in [2^60, 2^64): the same table
+// entries, their 53-bit mantissas multiplied in integers (three 64 x 64-bit
+// products, each truncated to its upper 64 bits; relative error below 2^-59),
+// so the selection needs no float64 arithmetic.  Where hop_rate_grid calls
+// exp (tables unusable, or the energy off their range) the float64 rate is
+// converted instead; a non-finite rate sets bad.
+__device__ __forceinline__ void hop_rate_fixed(const StepShared& S, const Dyn& D, int A, int q, bool etab_ok,
+                                               unsigned long long& M, int& E, int& bad) {
+    if (A == kVac) {
+        M = 0;
+        E = 0;
+        return;
+    }
+    const int Ai = A < 4 ? A : 3;
+    const bool zero = q < S.thr_lo[Ai], up = q > S.thr_hi[Ai];
+    const long long j = zero ? 0 : (up ? 2LL * q : (long long)q + (1LL << 26));
+    if (!etab_ok || !(j >= 0 && j < (1LL << 27))) {
+        const double g = hop_rate_grid(S, D, A, q);
+        bad |= !finite_bits(g);
+        rate_to_fixed(g, M, E);
+        return;
+    }
+    const int ji = (int)j;
+    const unsigned long long bK = (unsigned long long)__double_as_longlong((zero || up) ? S.nu : D.etab[1536 + Ai]);
+    const unsigned long long b0 = (unsigned long long)__double_as_longlong(D.etab[ji & 511]);
+    const unsigned long long b1 = (unsigned long long)__double_as_longlong(D.etab[512 + ((ji >> 9) & 511)]);
+    const unsigned long long b2 = (unsigned long long)__double_as_longlong(D.etab[1024 + (ji >> 18)]);
+    auto m11 = [](unsigned long long b) { return ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11; };
+    auto ex = [](unsigned long long b) { return (int)((b >> 52) & 0x7ff) - 1075; };
+    const unsigned long long a = __umul64hi(m11(bK), m11(b0));   // floor(mK m0 / 2^42) in [2^62, 2^64)
+    const unsigned long long c = __umul64hi(m11(b1), m11(b2));   // floor(m1 m2 / 2^42)
+    M = __umul64hi(a, c);                                        // floor(a c / 2^64) in [2^60, 2^64)
+    E = ex(bK) + ex(b0) + ex(b1) + ex(b2) + 148;
+}
+
 // Uniforms of event n built from the Philox block with integer operations
 // (exact: a 53-bit integer times 2^-53).
 __device__ __forceinline__ double u53_to_double(uint64_t a) {
@@ -378,7 +424,8 @@ __device__ __forceinline__ void next_uniforms(StepShared& S) {
         c3 = 0xC0000000u | ((uint32_t)uid & 0x3FFFFFFFu);
     }
     philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-    S.nu1 = u53_to_double(((uint64_t)c0 << 21) | (c1 >> 11));
+    S.nuU1 = ((uint64_t)c0 << 21) | (c1 >> 11);
+    S.nu1 = u53_to_double(S.nuU1);
     S.nu2 = u53_to_double((((uint64_t)c2 << 21) | (c3 >> 11)) + 1);
 }
 
@@ -1007,8 +1054,17 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
         dl0[j] = wdelta(0, o, W);
         dl1[j] = wdelta(1, o, W);
     }
+    // the lane holding the hop's own-embedding entry (one per hop)
+    bool own_lane = false;
+#pragma unroll
+    for (int j = 0; j < EJ; ++j) own_lane |= MODE != 0 && en[j] != 0xFFFFFFFFu && (en[j] >> 14);
     const int32_t omk = S.off[S.mk[k]];
     const int dm0 = wdelta(0, omk, W), dm1 = wdelta(1, omk, W);
+    // embedding of the read set's sites (split-precision EAM): thread u takes
+    // union site u around the vacancy
+    const bool sf_on = MODE != 0 && tid < kEamU;
+    const int32_t sfo = sf_on ? S.off[tid] : off_pack(0, 0, 0, 0);
+    const int sf0 = wdelta(0, sfo, W), sf1 = wdelta(1, sfo, W);
     const int mkk = S.mk[k];
     const EmbedC E = embed_consts(S);
     // per-thread constants of the density update: threads of the warps that do
@@ -1027,6 +1083,7 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
     int32_t* const log = S.v.log;
     uint8_t* const species = S.v.species;
     const int hi_edge = 2 * W - 5;
+    const bool etab_ok = S.v.etab_ok;
     __syncthreads();
 
     int ccount = S.ccount;
@@ -1044,45 +1101,80 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                 const int mwb = widx(mlX, mlY, mlZ, W);
                 const bool out = mlX < 4 || mlX > hi_edge || mlY < 4 || mlY > hi_edge || mlZ < 4 || mlZ > hi_edge;
                 const double u1 = S.nu1, u2 = S.nu2;
-                int A, dq = 0, bad;
-                double g;
-                if (first) {
-                    A = D.hop_sp[lane];
-                    g = D.rates[lane];
-                    bad = !finite_bits(g);
+                int A, dq = 0, bad, d = 0;
+                bool trapped;
+                double g = 0.0, R = 0.0;
+                if constexpr (WPH == 1) {
+                    // (a4)+(a6) in integers: the float64 rates, their sum for the clock
+                    // and the stored state come from warp 4 beside this chain
+                    unsigned long long M;
+                    int E;
+                    if (first) {
+                        A = D.hop_sp[lane];
+                        g = D.rates[lane];
+                        bad = !finite_bits(g);
+                        rate_to_fixed(g, M, E);
+                    } else {
+                        A = S.hsp[lane];
+                        dq = MODE == 0 ? S.acc32[lane] : (int)((S.acc64[0][lane] + S.acc64[1][lane] + (1LL << 15)) >> 16);
+                        bad = S.hbad[0][lane] | S.hbad[1][lane];
+                        hop_rate_fixed(S, D, A, dq, etab_ok, M, E, bad);
+                    }
+                    bad = __any_sync(0xffu, bad);
+                    // every rate on the scale of the largest (below 2^60, the others
+                    // truncated below 2^-60 of it), inclusive prefix sums over the lanes,
+                    // t = floor(u1 R), and the first lane whose prefix exceeds t: the
+                    // event the float64 tree descent picks unless t lies within rounding
+                    // of a boundary (a declared tie)
+                    const int Em = __reduce_max_sync(0xffu, M ? E : -(1 << 20));
+                    const int sh = Em - E + 4;
+                    unsigned long long P = (M == 0 || sh >= 64) ? 0ull : M >> sh;
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) {
+                        const unsigned long long x = __shfl_up_sync(0xffu, P, o);
+                        if (lane >= o) P += x;
+                    }
+                    const unsigned long long Rq = __shfl_sync(0xffu, P, 7);
+                    const unsigned long long tq = __umul64hi(S.nuU1 << 11, Rq);
+                    d = __ffs(__ballot_sync(0xffu, tq < P)) - 1;
+                    trapped = Rq == 0;
                 } else {
-                    A = S.hsp[lane];
-                    dq = MODE == 0 ? S.acc32[lane] : (int)((S.acc64[0][lane] + S.acc64[1][lane] + (1LL << 15)) >> 16);
-                    g = hop_rate_grid(S, D, A, dq);
-                    bad = S.hbad[0][lane] | S.hbad[1][lane] | !finite_bits(g);
+                    if (first) {
+                        A = D.hop_sp[lane];
+                        g = D.rates[lane];
+                        bad = !finite_bits(g);
+                    } else {
+                        A = S.hsp[lane];
+                        dq = MODE == 0 ? S.acc32[lane] : (int)((S.acc64[0][lane] + S.acc64[1][lane] + (1LL << 15)) >> 16);
+                        g = hop_rate_grid(S, D, A, dq);
+                        bad = S.hbad[0][lane] | S.hbad[1][lane] | !finite_bits(g);
+                    }
+                    const double s1 = g + __shfl_xor_sync(0xffu, g, 1);
+                    const double s2 = s1 + __shfl_xor_sync(0xffu, s1, 2);
+                    R = s2 + __shfl_xor_sync(0xffu, s2, 4);
+                    bad = __any_sync(0xffu, bad);
+                    // (a6) descent over the 3 levels of the vacancy's hop tree, the
+                    // compares and subtractions of the general path, in every lane
+                    double t = u1 * R;
+                    const double h2 = __shfl_sync(0xffu, s2, 0), h3 = __shfl_sync(0xffu, s2, 4);
+                    const double h4 = __shfl_sync(0xffu, s1, 0), h5 = __shfl_sync(0xffu, s1, 2);
+                    const double h6 = __shfl_sync(0xffu, s1, 4), h7 = __shfl_sync(0xffu, s1, 6);
+                    const double g0 = __shfl_sync(0xffu, g, 0), g1 = __shfl_sync(0xffu, g, 1);
+                    const double g2 = __shfl_sync(0xffu, g, 2), g3 = __shfl_sync(0xffu, g, 3);
+                    const double g4 = __shfl_sync(0xffu, g, 4), g5 = __shfl_sync(0xffu, g, 5);
+                    const double g6 = __shfl_sync(0xffu, g, 6), g7 = __shfl_sync(0xffu, g, 7);
+                    if (!(lt_nonneg(t, h2) || is_zero(h3))) { t -= h2; d = 4; }
+                    const double l2 = d ? h6 : h4, r2 = d ? h7 : h5;
+                    if (!(lt_nonneg(t, l2) || is_zero(r2))) { t -= l2; d += 2; }
+                    const double l3 = d == 0 ? g0 : d == 2 ? g2 : d == 4 ? g4 : g6;
+                    const double r3 = d == 0 ? g1 : d == 2 ? g3 : d == 4 ? g5 : g7;
+                    if (!(lt_nonneg(t, l3) || is_zero(r3))) d += 1;
+                    trapped = !(__double_as_longlong(R) > 0);
+                    // stored state of this event's rates (off the chain)
+                    D.rates[lane] = g;
+                    D.dE[lane] = (A == kVac || first) ? (first ? D.dE[lane] : 0.0) : q24_to_double(dq);
+                    D.hop_sp[lane] = (uint8_t)A;
                 }
-                const double s1 = g + __shfl_xor_sync(0xffu, g, 1);
-                const double s2 = s1 + __shfl_xor_sync(0xffu, s1, 2);
-                const double s3 = s2 + __shfl_xor_sync(0xffu, s2, 4);
-                bad = __any_sync(0xffu, bad);
-                // (a6) descent over the 3 levels of the vacancy's hop tree, the
-                // compares and subtractions of the general path, in every lane
-                const double R = s3;
-                double t = u1 * R;
-                const double h2 = __shfl_sync(0xffu, s2, 0), h3 = __shfl_sync(0xffu, s2, 4);
-                const double h4 = __shfl_sync(0xffu, s1, 0), h5 = __shfl_sync(0xffu, s1, 2);
-                const double h6 = __shfl_sync(0xffu, s1, 4), h7 = __shfl_sync(0xffu, s1, 6);
-                const double g0 = __shfl_sync(0xffu, g, 0), g1 = __shfl_sync(0xffu, g, 1);
-                const double g2 = __shfl_sync(0xffu, g, 2), g3 = __shfl_sync(0xffu, g, 3);
-                const double g4 = __shfl_sync(0xffu, g, 4), g5 = __shfl_sync(0xffu, g, 5);
-                const double g6 = __shfl_sync(0xffu, g, 6), g7 = __shfl_sync(0xffu, g, 7);
-                int d = 0;
-                if (!(lt_nonneg(t, h2) || is_zero(h3))) { t -= h2; d = 4; }
-                const double l2 = d ? h6 : h4, r2 = d ? h7 : h5;
-                if (!(lt_nonneg(t, l2) || is_zero(r2))) { t -= l2; d += 2; }
-                const double l3 = d == 0 ? g0 : d == 2 ? g2 : d == 4 ? g4 : g6;
-                const double r3 = d == 0 ? g1 : d == 2 ? g3 : d == 4 ? g5 : g7;
-                if (!(lt_nonneg(t, l3) || is_zero(r3))) d += 1;
-                // stored state of this event's rates (off the chain)
-                D.rates[lane] = g;
-                D.dE[lane] = (A == kVac || first) ? (first ? D.dE[lane] : 0.0) : q24_to_double(dq);
-                D.hop_sp[lane] = (uint8_t)A;
-                const bool trapped = !(__double_as_longlong(R) > 0);
                 const bool go = !finish && !bad && !S.numeric && !trapped;
                 if (go) {
                     // (a7) the move of lane d: vacancy w -> m, atom Ad m -> w
@@ -1106,7 +1198,7 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                         S.recenter = nout;
                         const int c = ccount;
                         S.cu2[c] = u2;
-                        S.cR[c] = R;
+                        if constexpr (WPH != 1) S.cR[c] = R;
                         if (log_cap > 0) log[n_ev % (uint64_t)log_cap] = d;
                     }
                     disp0 += (d & 1) ? -1 : 1;
@@ -1119,7 +1211,7 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                     n_ev += 1;
                 }
                 if (lane == 0) {
-                    D.tree[1] = R;
+                    if constexpr (WPH != 1) D.tree[1] = R;
                     if (bad) S.numeric = 1;
                     if (!finish && !go) {
                         S.v.status = (bad || S.numeric) ? kENUMERIC : kETRAPPED;
@@ -1140,6 +1232,31 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                 }
             }
         } else {
+            if constexpr (WPH == 1) {
+                if (warp == 4 && lane < 8) {
+                    // the float64 rates of this event (stored state), their sum for
+                    // the clock and the stored tree root, as the general path computes them
+                    double g;
+                    if (first) {
+                        g = D.rates[lane];
+                    } else {
+                        const int A = S.hsp[lane];
+                        const int dq = MODE == 0 ? S.acc32[lane]
+                                                 : (int)((S.acc64[0][lane] + S.acc64[1][lane] + (1LL << 15)) >> 16);
+                        g = hop_rate_grid(S, D, A, dq);
+                        D.rates[lane] = g;
+                        D.dE[lane] = A == kVac ? 0.0 : q24_to_double(dq);
+                        D.hop_sp[lane] = (uint8_t)A;
+                    }
+                    const double s1 = g + __shfl_xor_sync(0xffu, g, 1);
+                    const double s2 = s1 + __shfl_xor_sync(0xffu, s1, 2);
+                    const double R = s2 + __shfl_xor_sync(0xffu, s2, 4);
+                    if (lane == 0) {
+                        S.cR[ccount] = R;
+                        D.tree[1] = R;
+                    }
+                }
+            }
             if (upd && !first) {
                 // (a7) density change of the pending hop w -> m (atom pA now at w):
                 // rho_i += f_A(r_iw) over S(w), -= f_A(r_im) over S(m)
@@ -1157,7 +1274,8 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                 uint32_t c0 = (uint32_t)n_next, c1 = (uint32_t)(n_next >> 32), c2 = (uint32_t)uid,
                          c3 = (uint32_t)(uid >> 32) & 0x7fffffffu;
                 philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-                S.nx1 = u53_to_double(((uint64_t)c0 << 21) | (c1 >> 11));
+                S.nxU1 = ((uint64_t)c0 << 21) | (c1 >> 11);
+                S.nx1 = u53_to_double(S.nxU1);
                 S.nx2 = u53_to_double((((uint64_t)c2 << 21) | (c3 >> 11)) + 1);
             }
         }
@@ -1182,6 +1300,19 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
         const int b = S.lX & 1, base = S.wb;
         const int Ap = S.A, dp = S.dir;
         const int A = D.wsp[base + (b ? dm1 : dm0)];
+        if (MODE != 0) {
+            // F_{s_u}(rho_u) of every read-set site at its current density (the
+            // window lags by the hop just made; that hop's density change comes from
+            // the table), shared by the terms of all 8 hops
+            if (sf_on) {
+                const int wi = base + (b ? sf1 : sf0);
+                const int a = D.wsp[wi];
+                int fb = 0;
+                S.fsite[tid] = a != kVac ? embed_c(E, a, D.wrho[wi] + D.dprev[(dp * 4 + Ap) * kEamU + tid], fb) : 0;
+                S.fbad[tid] = (uint8_t)fb;
+            }
+            __syncthreads();
+        }
         if (MODE == 0) {
             int v = 0;
             if (A != kVac) {
@@ -1206,26 +1337,39 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
             if (A != kVac) {
                 const int* dpv = D.dprev + (dp * 4 + Ap) * kEamU;
                 const int32_t* fqA = S.fq[A];
+                // every load of this lane's entries first (independent chains), then
+                // the embedding differences (F at the changed density minus the site's
+                // F from the table above) and pair terms of the admissible ones
+                int ea[EJ], eu[EJ], es[EJ];
+                long long ph[EJ];
+                bool on[EJ];
 #pragma unroll
                 for (int j = 0; j < EJ; ++j) {
                     const uint32_t e = en[j];
-                    if (e == 0xFFFFFFFFu) continue;
-                    if (e >> 14) {
-                        // the moving atom's own embedding: F_A(rho_w - f_A(1nn)) - F_A(rho_m)
-                        const int rp = D.wrho[base] + dpv[0];
-                        const int rm = D.wrho[base + (b ? dm1 : dm0)] + dpv[mkk];
-                        v += embed_c(E, A, rp - S.fq[A][1], bad) - embed_c(E, A, rm, bad);
-                    } else {
-                        const int idx = e & 0xff, sip = (e >> 8) & 7, sim = (e >> 11) & 7;
-                        const int wi = base + (b ? dl1[j] : dl0[j]);
-                        const int a = D.wsp[wi];
-                        const int r = D.wrho[wi] + dpv[idx];
-                        const int dka = fqA[sip] - fqA[sim];
-                        if (a == kVac) continue;
-                        const int pi = pair_index(A, a);
-                        v += embed_c(E, a, r + dka, bad) - embed_c(E, a, r, bad) +
-                             (S.phi_q[pi][sip] - S.phi_q[pi][sim]);
+                    const bool site = e != 0xFFFFFFFFu && !(e >> 14);
+                    const int idx = site ? (int)(e & 0xff) : 0;
+                    const int sip = site ? (int)((e >> 8) & 7) : 0, sim = site ? (int)((e >> 11) & 7) : 0;
+                    const int wi = base + (b ? dl1[j] : dl0[j]);
+                    const int a = D.wsp[wi];
+                    const int r = D.wrho[wi] + dpv[idx];
+                    on[j] = site && a != kVac;
+                    es[j] = a;
+                    eu[j] = idx;
+                    ea[j] = r + (fqA[sip] - fqA[sim]);
+                    const int pi = pair_index(A, a < kVac ? a : 0);
+                    ph[j] = S.phi_q[pi][sip] - S.phi_q[pi][sim];
+                }
+#pragma unroll
+                for (int j = 0; j < EJ; ++j)
+                    if (on[j]) {
+                        v += embed_c(E, es[j], ea[j], bad) - S.fsite[eu[j]] + ph[j];
+                        bad |= S.fbad[eu[j]];
                     }
+                if (own_lane) {
+                    // the moving atom's own embedding: F_A(rho_w - f_A(1nn)) - F_A(rho_m)
+                    const int rp = D.wrho[base] + dpv[0];
+                    v += embed_c(E, A, rp - S.fq[A][1], bad) - S.fsite[mkk];
+                    bad |= S.fbad[mkk];
                 }
             }
             v = warp_sum_exact(v);
@@ -1242,6 +1386,7 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
         }
         if (tid == NT - 1) {
             S.nu1 = S.nx1;
+            S.nuU1 = S.nxU1;
             S.nu2 = S.nx2;
             // the hop just made becomes the pending density change (window sites
             // taken in the window as it is now, after any re-centring)
