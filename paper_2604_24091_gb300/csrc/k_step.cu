@@ -35,6 +35,7 @@
 namespace akmc {
 
 constexpr int kClockBatch = 128;
+constexpr long long kFBad = (long long)0x8000000000000000ull;   // window path: site embedding off the table
 
 struct __align__(16) StepShared {
     double E0[4];
@@ -48,6 +49,8 @@ struct __align__(16) StepShared {
     const long long* Fq;
     int32_t eps_q[2][25];
     int32_t fq[5][8];
+    int32_t dkq[4][64];       // fq[A][sip] - fq[A][sim] at index sip + 8 sim (window path)
+    long long dphi[10][64];   // phi_q[pi][sip] - phi_q[pi][sim] at index sip + 8 sim (window path)
     int32_t thr_hi[4], thr_lo[4];
     int32_t sph[64];
     int32_t off[160];
@@ -201,6 +204,14 @@ __device__ void load_model(StepShared& S, const ModelDev* M) {
     for (int i = tid; i < 80; i += NW * 32) {
         S.phi_d[i / 8][i % 8] = M->phi_d[i / 8][i % 8];
         S.phi_q[i / 8][i % 8] = M->phi_q[i / 8][i % 8];
+    }
+    for (int i = tid; i < 4 * 64; i += NW * 32) {
+        const int A = i >> 6, sp = i & 7, sm = (i >> 3) & 7;
+        S.dkq[A][i & 63] = M->fq[A][sp] - M->fq[A][sm];
+    }
+    for (int i = tid; i < 10 * 64; i += NW * 32) {
+        const int pi = i >> 6, sp = i & 7, sm = (i >> 3) & 7;
+        S.dphi[pi][i & 63] = M->phi_q[pi][sp] - M->phi_q[pi][sm];
     }
     if (tid < 4) {
         S.E0[tid] = M->E0[tid];
@@ -968,26 +979,46 @@ __device__ __forceinline__ void window_center(StepShared& S, int X, int Y, int Z
 }
 
 // All threads: load the window at the current origin (L2 loads that bypass L1,
-// so the density atomics of this CTA are seen).
+// so the density atomics of this CTA are seen).  One warp per window row
+// (cells y, z; its 2W sites are contiguous in the lattice unless x wraps), the
+// lanes over the row's sites, four rows in flight per warp.
 template <int NW, int MODE>
 __device__ void window_load(StepShared& S, const Dyn& D) {
-    constexpr int NT = NW * 32;
     const int W = S.W, L = S.v.L, ox = S.ox, oy = S.oy, oz = S.oz;
-    const int n = 2 * W * W * W;
+    const int M2 = 2 * L, W2 = 2 * W, RS = 2 * W + 1, PS = W * RS + 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t* sp = S.v.species;
     const int32_t* rho = S.v.rho;
-#pragma unroll 4
-    for (int j = threadIdx.x; j < n; j += NT) {
-        const int c = j >> 1, bb = j & 1;
-        const int lx = c % W, r = c / W, ly = r % W, lz = r / W;
-        int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-        gx -= gx >= L ? L : 0;
-        gy -= gy >= L ? L : 0;
-        gz -= gz >= L ? L : 0;
-        const size_t g = ((((size_t)gz * L + gy) * L + gx) << 1) | (size_t)bb;
-        const int w = widx(2 * lx + bb, 2 * ly + bb, 2 * lz + bb, W);
-        D.wsp[w] = __ldcg(sp + g);
-        if (MODE != 0) D.wrho[w] = __ldcg(rho + g);
+    // this lane's site of a row: cell lx = c / 2, parity c & 1, lattice x wrapped once
+    const int c = lane;
+    int gx = ox + (c >> 1);
+    gx -= gx >= L ? L : 0;
+    const int xoff = 2 * gx + (c & 1);
+    const bool on = c < W2;
+    const int n_rows = W * W;
+    for (int r0 = warp; r0 < n_rows; r0 += 4 * NW) {
+        uint8_t s4[4];
+        int32_t q4[4];
+        int w4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * NW;
+            const bool ok = on && r < n_rows;
+            const int ly = r % W, lz = r / W;
+            int gy = oy + ly, gz = oz + lz;
+            gy -= gy >= L ? L : 0;
+            gz -= gz >= L ? L : 0;
+            const size_t g = ((size_t)gz * L + gy) * M2 + xoff;
+            w4[u] = ok ? lz * PS + ly * RS + c : -1;
+            s4[u] = ok ? __ldcg(sp + g) : 0;
+            if (MODE != 0) q4[u] = ok ? __ldcg(rho + g) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (w4[u] >= 0) {
+                D.wsp[w4[u]] = s4[u];
+                if (MODE != 0) D.wrho[w4[u]] = q4[u];
+            }
     }
 }
 
@@ -1308,8 +1339,8 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                 const int wi = base + (b ? sf1 : sf0);
                 const int a = D.wsp[wi];
                 int fb = 0;
-                S.fsite[tid] = a != kVac ? embed_c(E, a, D.wrho[wi] + D.dprev[(dp * 4 + Ap) * kEamU + tid], fb) : 0;
-                S.fbad[tid] = (uint8_t)fb;
+                const long long f = a != kVac ? embed_c(E, a, D.wrho[wi] + D.dprev[(dp * 4 + Ap) * kEamU + tid], fb) : 0;
+                S.fsite[tid] = fb ? kFBad : f;      // a density off the table: flagged in the value
             }
             __syncthreads();
         }
@@ -1336,7 +1367,7 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
             int bad = 0;
             if (A != kVac) {
                 const int* dpv = D.dprev + (dp * 4 + Ap) * kEamU;
-                const int32_t* fqA = S.fq[A];
+                const int32_t* dkA = S.dkq[A];
                 // every load of this lane's entries first (independent chains), then
                 // the embedding differences (F at the changed density minus the site's
                 // F from the table above) and pair terms of the admissible ones
@@ -1348,28 +1379,29 @@ __device__ void run_events_window(StepShared& S, const Dyn& D, uint64_t target) 
                     const uint32_t e = en[j];
                     const bool site = e != 0xFFFFFFFFu && !(e >> 14);
                     const int idx = site ? (int)(e & 0xff) : 0;
-                    const int sip = site ? (int)((e >> 8) & 7) : 0, sim = site ? (int)((e >> 11) & 7) : 0;
+                    const int ss = site ? (int)((e >> 8) & 63) : 0;     // sip + 8 sim
                     const int wi = base + (b ? dl1[j] : dl0[j]);
                     const int a = D.wsp[wi];
                     const int r = D.wrho[wi] + dpv[idx];
                     on[j] = site && a != kVac;
                     es[j] = a;
                     eu[j] = idx;
-                    ea[j] = r + (fqA[sip] - fqA[sim]);
-                    const int pi = pair_index(A, a < kVac ? a : 0);
-                    ph[j] = S.phi_q[pi][sip] - S.phi_q[pi][sim];
+                    ea[j] = r + dkA[ss];
+                    ph[j] = S.dphi[pair_index(A, a < kVac ? a : 0)][ss];
                 }
 #pragma unroll
                 for (int j = 0; j < EJ; ++j)
                     if (on[j]) {
-                        v += embed_c(E, es[j], ea[j], bad) - S.fsite[eu[j]] + ph[j];
-                        bad |= S.fbad[eu[j]];
+                        const long long f = S.fsite[eu[j]];
+                        bad |= f == kFBad;
+                        v += embed_c(E, es[j], ea[j], bad) - (f == kFBad ? 0 : f) + ph[j];
                     }
                 if (own_lane) {
                     // the moving atom's own embedding: F_A(rho_w - f_A(1nn)) - F_A(rho_m)
                     const int rp = D.wrho[base] + dpv[0];
-                    v += embed_c(E, A, rp - S.fq[A][1], bad) - S.fsite[mkk];
-                    bad |= S.fbad[mkk];
+                    const long long f = S.fsite[mkk];
+                    bad |= f == kFBad;
+                    v += embed_c(E, A, rp - S.fq[A][1], bad) - (f == kFBad ? 0 : f);
                 }
             }
             v = warp_sum_exact(v);
