@@ -55,12 +55,12 @@ EAM_BYTES_PER_EVENT = 145 * (1 + 4) + 2 + 78 * 4 * 2
 RATE_BYTES_PER_SITE = 5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per event of one
 # full-size step-kernel launch, from one ncu capture of
-# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (696 MB read +
-# 5.39 GB written for 2.56e8 events), and warp instructions per event
+# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (1.006 GB read +
+# 5.342 GB written for 2.56e8 events), and warp instructions per event
 # (smsp__inst_executed.sum of the 2000-event case of the same workload);
 # valid only for the kernel source they were taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": "59c1ee62c3adf61a031e4b08f32b3c1e1822b2ed", "bytes_per_event": 23.79,
-                    "warp_inst_per_event": 4196}
+NCU_STEP_TRAFFIC = {"k_step_sha1": "3973371310f207aae49835868dccb9b70758f33b", "bytes_per_event": 24.80,
+                    "warp_inst_per_event": 3803}
 
 
 # DRAM bytes of one density_strip_kernel launch on the rate-kernel workload (300
