@@ -406,6 +406,10 @@ def large_run(model, torch, Batch, total=100_000_000, every=1_000_000):
         t_hist += time.perf_counter() - t0
         st = lb.read_state(0, species=False)
         clock.append(st["t_hi"] + st["t_lo"])
+        # one progress line per histogram (stderr), so a cut-off run keeps its series
+        sys.stderr.write(json.dumps({"events": st["n_events"], "step_seconds": t_step, "clock_s": clock[-1],
+                                     "hist": series[-1], "status": st["status"]}) + "\n")
+        sys.stderr.flush()
         if st["status"] != 0:
             break
     s = lb.read_state(0, species=False)

@@ -133,17 +133,20 @@ akmc_status akmc_create_batch(const akmc_voxel_desc* descs, int32_t n_voxels,
  * exact), then the 8 rates of every vacancy and the rate trees. */
 akmc_status akmc_compute_rates(akmc_batch* batch, akmc_stream stream);
 
-/* Run n_events[v] further events on every voxel v (host array of n_voxels
- * entries; copied before return).  One persistent launch steps all voxels;
+/* Run n_events[v] further events on every voxel v (n_voxels entries).  A host
+ * array is copied before return and sets the processing order (largest
+ * expected work first); a device array is copied on the stream (device to
+ * device) and the processing order of the previous call is kept (voxel order
+ * before any host call).  One persistent launch steps all voxels;
  * a voxel stops early when trapped or on a numeric error.  Results do not
  * depend on the batch composition or launch shape: each voxel's stream is
  * Philox(seed, (n, uid)). */
 akmc_status akmc_step_n(akmc_batch* batch, const uint64_t* n_events, akmc_stream stream);
 
 /* The two halves of akmc_step_n, for CUDA-graph capture and chunked serving:
- * akmc_set_targets copies n_events (host, n_voxels entries) and the processing
- * order into the workspace (stream-ordered; the host array may be reused on
- * return); akmc_launch_step resets the work queue and launches the persistent
+ * akmc_set_targets copies n_events (host or device, n_voxels entries, as for
+ * akmc_step_n) and the processing order into the workspace (stream-ordered;
+ * a host array may be reused on return); akmc_launch_step resets the work queue and launches the persistent
  * step kernel with the targets already on the device -- one memset and one
  * kernel, so a stream capture of it replays "run the stored targets again".
  * akmc_launch_step fails with AKMC_EINVAL while rates are out of date after

@@ -228,7 +228,15 @@ class Batch:
         _check(self._lib.akmc_compute_rates(self._h, _stream_ptr(stream)))
 
     def step(self, n_events, stream=None):
-        """Run n_events (scalar or one per voxel) further events per voxel."""
+        """Run n_events further events per voxel: a scalar or one per voxel (host),
+        or a contiguous CUDA int64 tensor of one count per voxel (device)."""
+        import torch
+        if isinstance(n_events, torch.Tensor):
+            if not (n_events.is_cuda and n_events.dtype == torch.int64 and n_events.is_contiguous()
+                    and n_events.numel() == self.n):
+                raise AkmcError(EINVAL, "device targets must be a contiguous CUDA int64 tensor of n_voxels entries")
+            _check(self._lib.akmc_step_n(self._h, ctypes.c_void_p(n_events.data_ptr()), _stream_ptr(stream)))
+            return
         arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n_events, np.uint64), (self.n,)))
         _check(self._lib.akmc_step_n(self._h, _ptr(arr), _stream_ptr(stream)))
 

@@ -636,6 +636,19 @@ akmc_status akmc_compute_rates(akmc_batch* b, akmc_stream stream) {
 akmc_status akmc_set_targets(akmc_batch* b, const uint64_t* n_events, akmc_stream stream) {
     if (!b || !n_events) return fail(AKMC_EINVAL, "batch or n_events is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        // a device (or managed) array: copied on the stream, processing order kept
+        cudaPointerAttributes at{};
+        const cudaError_t pe = cudaPointerGetAttributes(&at, n_events);
+        if (pe != cudaSuccess) cudaGetLastError();
+        if (pe == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+            AKMC_CUDA(cudaMemcpyAsync(b->base + b->lo.targets, n_events, sizeof(uint64_t) * b->n,
+                                      cudaMemcpyDeviceToDevice, s));
+            if (b->occupancy[b->warps] == 0)
+                b->occupancy[b->warps] = step_occupancy(b->warps, b->lo.max_nv, b->lo.max_P, b->lo.win);
+            return AKMC_OK;
+        }
+    }
     const int slot = b->stage;
     b->stage = (b->stage + 1) % akmc_batch::kStage;
     if (b->staging_used[slot]) AKMC_CUDA(cudaEventSynchronize(b->staging_done[slot]));

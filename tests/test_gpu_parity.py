@@ -427,3 +427,20 @@ def test_arrhenius_temperature_sensitivity_on_gpu(model, mdl, prec):
     np.testing.assert_allclose(slope, Ea[live] / (synth.KB_EV * T * T), rtol=1e-6)
     assert (rates[1][~live] == 0).all()
     b.close()
+
+
+def test_device_targets_equal_host_targets(model):
+    # per-voxel targets from a device array (copied on the stream) give the same
+    # trajectories as the same targets from the host
+    descs = _mixed_descs()
+    tg = np.array([400, 0, 900, 250, 600, 300, 150], np.uint64)
+    a = Batch(descs, model, event_log_capacity=1000)
+    b = Batch(descs, model, event_log_capacity=1000)
+    a.step(tg)
+    b.step(torch.tensor(tg.astype(np.int64), device="cuda"))
+    for v in range(len(descs)):
+        sa, sb = a.read_state(v, log=True), b.read_state(v, log=True)
+        assert sa["n_events"] == sb["n_events"] == int(tg[v])
+        assert np.array_equal(sa["event_log"], sb["event_log"])
+        assert np.array_equal(sa["species"], sb["species"])
+        assert sa["t_hi"] == sb["t_hi"] and sa["t_lo"] == sb["t_lo"]
