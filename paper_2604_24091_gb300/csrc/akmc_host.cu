@@ -360,6 +360,9 @@ Layout make_layout(const akmc_voxel_desc* d, int32_t n, const akmc_model* m, int
         size_t N = 2 * (size_t)d[v].L * d[v].L * d[v].L;
         int nv = d[v].n_vac, P = next_pow2(nv);
         Lo.max_nv = std::max(Lo.max_nv, nv);
+        // a single vacancy in a lattice too small for the one-vacancy fast path
+        // (L < 6) takes the general path, whose staging the layout sizes for max_nv > 1
+        if (nv == 1 && d[v].L < 6) Lo.max_nv = std::max(Lo.max_nv, 2);
         Lo.max_P = std::max(Lo.max_P, P);
         Lo.win = std::max(Lo.win, window_edge(d[v].L, nv, d[v].model, d[v].precision));
         Lo.max_N = std::max(Lo.max_N, N);

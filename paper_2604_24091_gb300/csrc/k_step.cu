@@ -105,6 +105,20 @@ struct __align__(16) StepShared {
     double sl_t, sl_T;
 };
 
+// Staging of one vacancy's read set and hop sums, for the general path's
+// refresh of several vacancies per pass (kG at a time).
+constexpr int kG = 4;
+struct __align__(16) Grp {
+    long long fsite[kEamU];   // split precision: F_{s_u}(rho_u) in 2^-40 eV
+    int32_t srho[kEamU];
+    long long acc64[2][8];
+    double hop_de[8];
+    int32_t acc32[8];
+    int32_t hop_bad[8];
+    uint8_t ssp[kEamU];
+    uint8_t fbad[kEamU];
+};
+
 struct Dyn {
     double* tree;
     double* rates;
@@ -126,13 +140,14 @@ struct Dyn {
     int32_t* apos;    // sublattice superstep: packed half-unit coordinates of every vacancy at the start
     int32_t* lmap;    // sublattice superstep: local index of every vacancy, -1 if not local
     int32_t* fr;      // sublattice superstep: local vacancy's stored rates are current
+    Grp* grp;         // general path with several vacancies: kG staging blocks
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Offsets of the dynamic shared-memory arrays (16-byte aligned).
 struct DynLayout {
-    size_t off[20];
+    size_t off[21];
     size_t total;
 };
 
@@ -140,7 +155,7 @@ __host__ __device__ inline int win_sites(int W);
 
 __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) {
     const size_t nw = win > 0 ? (size_t)win_sites(win) : 0;
-    const size_t sz[20] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
+    const size_t sz[21] = {sizeof(double) * 2 * max_P, sizeof(double) * 8 * max_nv,
                            sizeof(double) * 8 * max_nv, sizeof(double) * 8 * max_nv,
                            sizeof(double) * kEtab,      sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
@@ -150,10 +165,10 @@ __host__ __device__ inline DynLayout dyn_layout(int max_nv, int max_P, int win) 
                            win > 0 ? sizeof(int32_t) * kEamU * 32 : 0,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
                            sizeof(int32_t) * max_nv,    sizeof(int32_t) * max_nv,
-                           sizeof(int32_t) * max_nv};
+                           sizeof(int32_t) * max_nv,    max_nv > 1 ? sizeof(Grp) * kG : 0};
     DynLayout l;
     size_t o = 0;
-    for (int i = 0; i < 20; ++i) {
+    for (int i = 0; i < 21; ++i) {
         l.off[i] = o;
         o = align16(o + sz[i]);
     }
@@ -184,6 +199,7 @@ __device__ __forceinline__ Dyn carve(unsigned char* base, int max_nv, int max_P,
     d.apos = (int32_t*)(base + l.off[17]);
     d.lmap = (int32_t*)(base + l.off[18]);
     d.fr = (int32_t*)(base + l.off[19]);
+    d.grp = max_nv > 1 ? (Grp*)(base + l.off[20]) : nullptr;
     return d;
 }
 
@@ -688,6 +704,222 @@ __device__ __forceinline__ void phase_rates(StepShared& S, const Dyn& D, int q) 
     __syncwarp();
 }
 
+// ---- general path, several vacancies per pass --------------------------------
+// After a hop the rates of the moved vacancy and of every vacancy within reach
+// of it are recomputed together, kG vacancies per pass: the read sets are
+// gathered from memory (the hop's density updates are already there), then
+// site embeddings, hop terms and rates run over all of them at once, so a pass
+// costs the barriers of one vacancy whatever the number refreshed.  The
+// arithmetic of every vacancy is that of the one-vacancy phases above.
+
+// (a7) the hop's density updates (rho_i += f_A(r_iw) over S(w), -= f_A(r_im)
+// over S(m)) and the list of other vacancies whose read set may contain a
+// changed site (every vacancy within `reach` half units of w per axis).
+template <int NW, int MODE>
+__device__ __forceinline__ void phase_hop_update(StepShared& S, const Dyn& D) {
+    constexpr int NT = NW * 32;
+    constexpr int reach = MODE != 0 ? 8 : 4;
+    const int tid = threadIdx.x;
+    const int L = S.v.L, M2 = 2 * L;
+    if (tid == NT - 1) next_uniforms(S);   // the next event's Philox block
+    if (MODE != 0) {
+        for (int i = tid; i < 2 * kSph; i += NT) {
+            const int side = i >= kSph;
+            const int o = S.sph[side ? i - kSph : i];
+            const int cX = side ? S.mX : S.wX, cY = side ? S.mY : S.wY, cZ = side ? S.mZ : S.wZ;
+            const int s = site_index(wrap_coord(cX + off_dx(o), M2), wrap_coord(cY + off_dy(o), M2),
+                                     wrap_coord(cZ + off_dz(o), M2), L);
+            const int f = S.fq[S.A][off_extra(o)];
+            atomicAdd(&S.v.rho[s], side ? -f : f);
+        }
+    }
+    for (int q = tid; q < S.v.nv; q += NT) {
+        if (q == S.slot) continue;
+        int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
+        ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
+        ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
+        ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
+        if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach) D.aff[atomicAdd(&S.n_aff, 1)] = q;
+    }
+}
+
+// vacancy of entry g0 + g of the refresh list: the moved one first
+__device__ __forceinline__ int grp_vacancy(const StepShared& S, const Dyn& D, int i) {
+    return i == 0 ? S.slot : D.aff[i - 1];
+}
+
+template <int NW, int MODE>
+__device__ __forceinline__ void grp_gather(StepShared& S, const Dyn& D, int g0, int n) {
+    constexpr int NT = NW * 32;
+    constexpr int U = MODE != 0 ? kEamU : kPairU;
+    const int tid = threadIdx.x;
+    const int L = S.v.L, M2 = 2 * L;
+    for (int i = tid; i < n * U; i += NT) {
+        const int g = i / U, u = i - g * U;
+        const int q = grp_vacancy(S, D, g0 + g);
+        const int o = S.off[u];
+        const int s = site_index(wrap_coord(D.X[q] + off_dx(o), M2), wrap_coord(D.Y[q] + off_dy(o), M2),
+                                 wrap_coord(D.Z[q] + off_dz(o), M2), L);
+        Grp& G = D.grp[g];
+        G.ssp[u] = S.v.species[s];
+        if (MODE != 0) G.srho[u] = S.v.rho[s];
+    }
+    for (int i = tid; i < n * 8; i += NT) {
+        Grp& G = D.grp[i >> 3];
+        G.acc64[0][i & 7] = 0;
+        G.acc64[1][i & 7] = 0;
+        G.acc32[i & 7] = 0;
+        G.hop_bad[i & 7] = 0;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void grp_site_embed(StepShared& S, const Dyn& D, int n) {
+    for (int i = threadIdx.x; i < n * kEamU; i += NW * 32) {
+        const int g = i / kEamU, u = i - g * kEamU;
+        Grp& G = D.grp[g];
+        const int a = G.ssp[u];
+        int bad = 0;
+        G.fsite[u] = a == kVac ? 0 : embed_q(S, a, G.srho[u], bad);
+        G.fbad[u] = (uint8_t)bad;
+    }
+}
+
+template <int NW, int MODE>
+__device__ __forceinline__ void grp_terms(StepShared& S, const Dyn& D, int n) {
+    constexpr int NT = NW * 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (MODE == 0) {
+        for (int it = tid; it < n * 8 * kPairE; it += NT) {
+            const int g = it / (8 * kPairE), r = it - g * 8 * kPairE, k = r / kPairE, e = r - k * kPairE;
+            Grp& G = D.grp[g];
+            const int A = G.ssp[S.mk[k]];
+            if (A == kVac) continue;
+            const uint32_t en = S.ent[k][e];
+            const int x = G.ssp[en & 0xff], sh = (en >> 8) & 1;
+            const int t = S.eps_q[sh][A * 5 + x] - S.eps_q[sh][kVac * 5 + x];
+            atomicAdd(&G.acc32[k], (en >> 9) & 1 ? -t : t);
+        }
+    } else if (MODE == 1) {
+        constexpr int WPH = NW >= 16 ? 2 : 1;
+        for (int kk = warp; kk < n * 8 * WPH; kk += NW) {
+            const int g = kk / (8 * WPH), r = kk - g * 8 * WPH, k = r & 7, half = r >> 3;
+            Grp& G = D.grp[g];
+            const int A = G.ssp[S.mk[k]];
+            if (A == kVac) continue;
+            long long v = 0;
+            int bad = 0;
+            for (int e = half * 32 + lane; e < kEamE; e += 32 * WPH) {
+                const uint32_t en = S.ent[k][e];
+                if (en >> 14) {
+                    const int mk = S.mk[k];
+                    v += embed_q(S, A, G.srho[0] - S.fq[A][1], bad) - G.fsite[mk];
+                    bad |= G.fbad[mk];
+                } else {
+                    const int idx = en & 0xff, sip = (en >> 8) & 7, sim = (en >> 11) & 7;
+                    const int a = G.ssp[idx];
+                    if (a == kVac) continue;
+                    const int pi = pair_index(A, a);
+                    v += embed_q(S, a, G.srho[idx] + S.fq[A][sip] - S.fq[A][sim], bad) - G.fsite[idx] +
+                         (S.phi_q[pi][sip] - S.phi_q[pi][sim]);
+                    bad |= G.fbad[idx];
+                }
+            }
+            v = warp_sum(v);
+            bad = __any_sync(0xffffffffu, bad);
+            if (lane == 0) {
+                G.acc64[half][k] = v;
+                if (bad) G.hop_bad[k] = 1;
+            }
+        }
+    } else {
+        for (int kk = warp; kk < n * 8; kk += NW) {
+            const int g = kk >> 3, k = kk & 7;
+            Grp& G = D.grp[g];
+            const int A = G.ssp[S.mk[k]];
+            if (A == kVac) {
+                if (lane == 0) G.hop_de[k] = 0.0;
+                continue;
+            }
+            double acc = 0.0;
+            int bad = 0;
+            for (int j = lane; j < kEamE; j += 32) {
+                const uint32_t en = S.ent[k][j];
+                int a, r0, r1;
+                double ph = 0.0;
+                if (en >> 14) {
+                    a = A;
+                    r0 = G.srho[S.mk[k]];
+                    r1 = G.srho[0] - S.fq[A][1];
+                } else {
+                    const int idx = en & 0xff, sip = (en >> 8) & 7, sim = (en >> 11) & 7;
+                    a = G.ssp[idx];
+                    if (a == kVac) continue;
+                    r0 = G.srho[idx];
+                    r1 = r0 + S.fq[A][sip] - S.fq[A][sim];
+                    const int pi = pair_index(A, a);
+                    ph = S.phi_d[pi][sip] - S.phi_d[pi][sim];
+                }
+                acc += (embed_fp64(S, a, r1, bad) - embed_fp64(S, a, r0, bad)) + ph;
+            }
+            acc = warp_sum(acc);
+            bad = __any_sync(0xffffffffu, bad);
+            if (lane == 0) {
+                G.hop_de[k] = acc;
+                G.hop_bad[k] = bad;
+            }
+        }
+    }
+}
+
+// R for up to kG vacancies at once: lane 8g + k takes hop k of vacancy g (the
+// arithmetic of phase_rates), then lane 0 updates the tree paths one after the
+// other.  Only warp 0 executes this; it ends with __syncwarp.
+template <int MODE>
+__device__ __forceinline__ void grp_rates(StepShared& S, const Dyn& D, int g0, int n) {
+    const int lane = threadIdx.x & 31, g = lane >> 3, k = lane & 7;
+    const bool on = g < n;
+    const int q = on ? grp_vacancy(S, D, g0 + g) : 0;
+    const Grp& G = D.grp[on ? g : 0];
+    const int A = G.ssp[S.mk[k]];
+    double de, gr;
+    if (MODE == 2) {
+        de = G.hop_de[k];
+        gr = hop_rate_fp64(S, D, A, de);
+    } else {
+        const int dq = MODE == 0 ? G.acc32[k] : (int)((G.acc64[0][k] + G.acc64[1][k] + (1LL << 15)) >> 16);
+        de = A == kVac ? 0.0 : (double)dq * 0x1p-24;
+        gr = hop_rate_grid(S, D, A, dq);
+    }
+    const int bad = on && (G.hop_bad[k] | !finite_bits(gr));
+    const double s1 = gr + __shfl_xor_sync(0xffffffffu, gr, 1);
+    const double s2 = s1 + __shfl_xor_sync(0xffffffffu, s1, 2);
+    const double s3 = s2 + __shfl_xor_sync(0xffffffffu, s2, 4);
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    if (on) {
+        D.rates[8 * q + k] = gr;
+        D.dE[8 * q + k] = de;
+        D.hop_sp[8 * q + k] = (uint8_t)A;
+        double* h = D.hsum + 8 * q;
+        if ((k & 1) == 0) h[4 + (k >> 1)] = s1;
+        if ((k & 3) == 0) h[2 + (k >> 2)] = s2;
+        if (k == 0) {
+            h[1] = s3;
+            D.tree[S.v.P + q] = s3;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int P = S.v.P;
+        for (int gg = 0; gg < n; ++gg) {
+            const int qq = grp_vacancy(S, D, g0 + gg);
+            for (int i = (P + qq) >> 1; i >= 1; i >>= 1) D.tree[i] = D.tree[2 * i] + D.tree[2 * i + 1];
+        }
+        if (anybad) S.numeric = 1;
+    }
+    __syncwarp();
+}
+
 // Full refresh of one vacancy with barriers (rebuild, and vacancies other
 // than the moved one).
 template <int NW, int MODE>
@@ -871,8 +1103,7 @@ __device__ __forceinline__ bool select_and_swap(StepShared& S, const Dyn& D) {
 template <int NW, int MODE>
 __device__ void run_events(StepShared& S, const Dyn& D, uint64_t target) {
     const int tid = threadIdx.x;
-    const int L = S.v.L, M2 = 2 * L;
-    constexpr int reach = MODE != 0 ? 8 : 4;
+    const int L = S.v.L;
     int ccount = S.ccount;   // uniform copy of the clock-batch fill
     const bool fast = S.v.nv == 1 && L >= (MODE != 0 ? 6 : 5);
     if (fast) {
@@ -887,33 +1118,29 @@ __device__ void run_events(StepShared& S, const Dyn& D, uint64_t target) {
         if (fast) {
             phase_fill<NW, MODE>(S);
             __syncthreads();
+            phase_terms<NW, MODE>(S, true);
+            __syncthreads();
+            if (tid < 32) phase_rates<MODE>(S, D, S.slot);
+            phase_prefetch<NW, MODE>(S, D, NW > 1 ? 32 : 0);
         } else {
-            // (a8) other vacancies whose read set may contain a changed site: every
-            // vacancy within `reach` half units of w per axis.
-            for (int q = tid; q < S.v.nv; q += NW * 32) {
-                if (q == S.slot) continue;
-                int ddx = D.X[q] - S.wX, ddy = D.Y[q] - S.wY, ddz = D.Z[q] - S.wZ;
-                ddx = ddx >= L ? ddx - M2 : (ddx < -L ? ddx + M2 : ddx);
-                ddy = ddy >= L ? ddy - M2 : (ddy < -L ? ddy + M2 : ddy);
-                ddz = ddz >= L ? ddz - M2 : (ddz < -L ? ddz + M2 : ddz);
-                if (abs(ddx) <= reach && abs(ddy) <= reach && abs(ddz) <= reach)
-                    D.aff[atomicAdd(&S.n_aff, 1)] = q;
-            }
-            phase_gather<NW, MODE>(S, D, S.slot, true);
+            // (a7) the hop's density updates and (a8) the refresh list, then the
+            // moved vacancy and every vacancy within reach, kG per pass
+            phase_hop_update<NW, MODE>(S, D);
             __syncthreads();
-            if (MODE == 1) {
-                phase_site_embed<NW>(S);
+            const int n_all = 1 + S.n_aff;
+            for (int g0 = 0; g0 < n_all; g0 += kG) {
+                const int n = min(kG, n_all - g0);
+                grp_gather<NW, MODE>(S, D, g0, n);
                 __syncthreads();
+                if (MODE == 1) {
+                    grp_site_embed<NW>(S, D, n);
+                    __syncthreads();
+                }
+                grp_terms<NW, MODE>(S, D, n);
+                __syncthreads();
+                if (tid < 32) grp_rates<MODE>(S, D, g0, n);
+                if (g0 + kG < n_all) __syncthreads();
             }
-        }
-        phase_terms<NW, MODE>(S, true);
-        __syncthreads();
-        if (tid < 32) phase_rates<MODE>(S, D, S.slot);
-        if (fast) phase_prefetch<NW, MODE>(S, D, NW > 1 ? 32 : 0);
-        const int n_aff = fast ? 0 : S.n_aff;
-        if (n_aff > 0) {
-            __syncthreads();
-            for (int i = 0; i < n_aff; ++i) refresh_full<NW, MODE>(S, D, D.aff[i]);
         }
         if (ccount == kClockBatch) {
             flush_clock<NW>(S);
