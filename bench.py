@@ -55,18 +55,18 @@ EAM_BYTES_PER_EVENT = 145 * (1 + 4) + 2 + 78 * 4 * 2
 RATE_BYTES_PER_SITE = 5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per event of one
 # full-size step-kernel launch, from one ncu capture of
-# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (1.006 GB read +
-# 5.342 GB written for 2.56e8 events), and warp instructions per event
-# (smsp__inst_executed.sum of the 2000-event case of the same workload);
+# `bench.py --steps 3 --warmup 3 --no-extras --launch 8,0` (0.687 GB read +
+# 5.291 GB written for 2.56e8 events), and warp instructions per event
+# (smsp__inst_executed.sum 1.949e9 of the 2000-event case of the same workload);
 # valid only for the kernel source they were taken from.
-NCU_STEP_TRAFFIC = {"k_step_sha1": "3973371310f207aae49835868dccb9b70758f33b", "bytes_per_event": 24.80,
-                    "warp_inst_per_event": 3803}
+NCU_STEP_TRAFFIC = {"k_step_sha1": "999ac0a3ea624035118fbafb4dfe50ac29eecebe", "bytes_per_event": 23.35,
+                    "warp_inst_per_event": 3807}
 
 
 # DRAM bytes of one density_strip_kernel launch on the rate-kernel workload (300
 # EAM voxels of 64^3 cells): 167 MB read + 569 MB written, from one ncu capture
 # of `bench.py --rate-kernel`; valid only for the kernel source it was taken from.
-NCU_RATE_TRAFFIC = {"k_density_sha1": "f9c23584f4b6205e6bb666bb96971f85260d47d0", "bytes": 736e6}
+NCU_RATE_TRAFFIC = {"k_density_sha1": "0c17618c42557127bfeb82c64bc81b39125d1dc3", "bytes": 736.4e6}
 
 
 def _src_sha1(name):
@@ -414,7 +414,7 @@ def large_run(model, torch, Batch, total=100_000_000, every=1_000_000):
             break
     s = lb.read_state(0, species=False)
     lb.close()
-    return {"config": "1 voxel of 128^3 cells (4194304 sites), Fe-0.2Cu-0.7Ni-1.4Mn at%, 64 vacancies, EAM split, "
+    return {"config": "1 voxel of 128^3 cells (4194304 sites), Fe-0.2Cu-0.7Ni-1.4Mn at%%, 64 vacancies, EAM split, "
                       "%d events, Cu-cluster histogram every %d events" % (total, every),
             "events": s["n_events"], "status": s["status"], "value": s["n_events"] / t_step, "unit": UNIT,
             "step_seconds": t_step, "histogram_ms_mean": 1e3 * t_hist / max(1, len(series)),

@@ -16,6 +16,8 @@
 #include "akmc_device.cuh"
 #include "akmc_launch.h"
 
+#include <utility>
+
 namespace akmc {
 
 constexpr int kDensThreads = 256;
@@ -161,6 +163,8 @@ __host__ __device__ inline size_t strip_smem(int TY, int L) {
 }
 // rows per strip: 16 for L <= 64, 8 for L <= 128, 2 beyond (shared memory and kChunks)
 __host__ __device__ inline int strip_rows(int L) { return L <= 64 ? 16 : (L <= 128 ? 8 : 2); }
+// edge of the fixed buffer geometry of the 16-byte path (L <= 128)
+__host__ __device__ inline int strip_geom_L(int L) { return L <= 32 ? 32 : (L <= 64 ? 64 : 128); }
 
 // floor((b + d) / 2) for b in {0,1}, d in [-4, 4]
 __device__ __forceinline__ int half_floor(int v) { return (v + 8) / 2 - 4; }
@@ -408,25 +412,269 @@ __device__ void strip_body(const VoxelDev& V, const int4 it, int32_t* buf, uint3
     }
 }
 
+// ---- fixed-geometry strip path (16-byte rows, L <= 128) ------------------------
+// The same strip walk with the buffer geometry fixed at compile time (row
+// stride 2 LG + 8, LG in {32, 64, 128} the smallest one >= L, TYG rows per
+// strip), so every stencil offset is an immediate in the reduction's address.
+// Scatter: one list entry per lane, 32 entries per warp pass; a lane adds its
+// entry's 58 weights with 58 reductions at [entry + constant] (halo-row entries
+// predicate each term on its target row).  Row pads fold into the row ends in
+// the write-out itself, and the write-out of a block shares its phase with the
+// list building of the next one: two CTA barriers per block of 4 planes.
+
+// The 58 cutoff-sphere offsets (half units) and their shells, in a fixed order.
+struct StencilTab {
+    int dx[kSph], dy[kSph], dz[kSph], sh[kSph];
+};
+constexpr StencilTab make_stencil() {
+    StencilTab t{};
+    int n = 0;
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+                const int q = dx * dx + dy * dy + dz * dz;
+                const int sh = q == 3 ? 1 : q == 4 ? 2 : q == 8 ? 3 : q == 11 ? 4 : q == 12 ? 5 : 0;
+                if (sh == 0 || ((dx ^ dy) & 1) || ((dy ^ dz) & 1)) continue;
+                t.dx[n] = dx, t.dy[n] = dy, t.dz[n] = dz, t.sh[n] = sh;
+                ++n;
+            }
+    return t;
+}
+constexpr StencilTab kStencil = make_stencil();
+constexpr int hfloor_c(int v) { return (v + 8) / 2 - 4; }
+// Offset K seen from a sublattice-B site in a buffer of row stride RW and plane
+// stride SLOT: its shell, its cell row offset and its buffer-word delta, all
+// compile-time constants.
+template <int B, int RW, int SLOT, int K>
+struct StOff {
+    static constexpr int sh = kStencil.sh[K];
+    static constexpr int dyc = hfloor_c(B + kStencil.dy[K]);
+    static constexpr int delta = hfloor_c(B + kStencil.dz[K]) * SLOT + dyc * RW + kStencil.dx[K];
+};
+template <int B, int RW, int SLOT>
+constexpr int st_min_f() {
+    int m = 0;
+    for (int k = 0; k < kSph; ++k) {
+        const int d = hfloor_c(B + kStencil.dz[k]) * SLOT + hfloor_c(B + kStencil.dy[k]) * RW + kStencil.dx[k];
+        m = d < m ? d : m;
+    }
+    return m;
+}
+template <int B, int RW, int SLOT>
+struct StMin {
+    static constexpr int v = st_min_f<B, RW, SLOT>();     // most negative delta
+};
+
+template <int D>
+__device__ __forceinline__ void red_imm(uint32_t a, int v) {
+    asm volatile("red.shared.add.s32 [%0+%1], %2;" ::"r"(a), "n"(D), "r"(v) : "memory");
+}
+// a = byte address of the entry's site + 4 StMin (every immediate is >= 0)
+template <int B, int RW, int SLOT, int... K>
+__device__ __forceinline__ void fx_own(uint32_t a, const int (&w)[6], std::integer_sequence<int, K...>) {
+    (red_imm<4 * (StOff<B, RW, SLOT, K>::delta - StMin<B, RW, SLOT>::v)>(a, w[StOff<B, RW, SLOT, K>::sh]), ...);
+}
+// halo-row entry: the term lands in the strip iff h + dyc < ty (h = halo row - 2, unsigned)
+template <int B, int RW, int SLOT, int... K>
+__device__ __forceinline__ void fx_halo(uint32_t a, const int (&w)[6], uint32_t h, uint32_t ty,
+                                        std::integer_sequence<int, K...>) {
+    ((h + (uint32_t)(int)StOff<B, RW, SLOT, K>::dyc < ty
+          ? red_imm<4 * (StOff<B, RW, SLOT, K>::delta - StMin<B, RW, SLOT>::v)>(a, w[StOff<B, RW, SLOT, K>::sh])
+          : void()),
+     ...);
+}
+
+template <int LG, int TYG>
+__device__ void strip_fast(const VoxelDev& V, const int4 it, int32_t* buf, uint32_t* lists,
+                           const int (*cq8)[8], const int32_t* sph, int* cnt2, int32_t rho0) {
+    constexpr int RW = 2 * LG + 2 * kRowPad, SLOT = (TYG + 2 * kGuard) * RW + 4;
+    using Seq = std::make_integer_sequence<int, kSph>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = V.L, M2 = 2 * L, nq = M2 / 4;
+    const int y0 = it.y, z0 = it.z, tz = it.w & 0xFFFF;
+    const int ty = min(TYG, L - y0);
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+    for (int pr = warp; pr < kPlanes * (ty + 2 * kGuard); pr += kStripThreads / 32) {
+        const int p = pr / (ty + 2 * kGuard), br = pr - p * (ty + 2 * kGuard);
+        int32_t* row = buf + p * SLOT + br * RW;
+        const bool own = br >= kGuard && br < ty + kGuard;
+        for (int c = lane; c < RW; c += 32) row[c] = own && c >= kRowPad && c < kRowPad + M2 ? rho0 : 0;
+    }
+    auto wrap = [&](int z) { return z < 0 ? z + L : (z >= L ? z - L : z); };
+    const int n_src = tz + 4;
+    const int cpr = M2 / 16, per_plane = (ty + 4) * cpr;
+    int ck_pl[kChunks], ck_hr[kChunks], ck_u[kChunks], ck_off[kChunks];
+#pragma unroll
+    for (int k = 0; k < kChunks; ++k) {
+        const int c = tid + k * kStripThreads;
+        const int pl = c / per_plane, rem = c - pl * per_plane;
+        const int hr = rem / cpr, cx = rem - hr * cpr;
+        ck_pl[k] = pl;
+        ck_hr[k] = hr;
+        ck_u[k] = (pl + 2) * SLOT + hr * RW + 16 * cx + kRowPad;
+        ck_off[k] = wrap(y0 - 2 + hr) * M2 + 16 * cx;
+    }
+    uint4 v[kChunks];
+    auto load_block = [&](int rb) {
+        const int nb = min(kBlk, n_src - rb);
+#pragma unroll
+        for (int k = 0; k < kChunks; ++k)
+            if (ck_pl[k] < nb)
+                v[k] = __ldcs((const uint4*)(V.species + (size_t)wrap(z0 - 2 + rb + ck_pl[k]) * L * M2 + ck_off[k]));
+    };
+    // list building of the block at rb (its chunks are in v), into counters cnt
+    auto append = [&](int rb, int* cnt) {
+        const int nb = min(kBlk, n_src - rb);
+#pragma unroll
+        for (int k = 0; k < kChunks; ++k) {
+            if (ck_pl[k] >= nb) break;
+            uint32_t M = nonzero_bytes(v[k]);
+            if (!M) continue;
+            const int hr = ck_hr[k];
+            const bool own = strip_own(hr, ty);
+            const uint32_t M0 = M & 0x5555u, M1 = M & 0xAAAAu;
+            int a0 = M0 ? atomicAdd(&cnt[own ? 0 : 1], __popc(M0)) : 0;
+            int a1 = M1 ? atomicAdd(&cnt[own ? 2 : 3], __popc(M1)) : 0;
+            while (M) {
+                const int j = __ffs(M) - 1;
+                M &= M - 1;
+                const uint32_t wj = j < 8 ? (j < 4 ? v[k].x : v[k].y) : (j < 12 ? v[k].z : v[k].w);
+                const uint32_t en = strip_entry((wj >> (8 * (j & 3))) & 0xFFu, ck_u[k] + j, hr);
+                if (j & 1) strip_push(lists, en, 1, own, a1++);
+                else strip_push(lists, en, 0, own, a0++);
+            }
+        }
+    };
+    if (tid < 8) cnt2[tid] = 0;
+    load_block(0);
+    __syncthreads();
+    append(0, cnt2);
+    if (kBlk < n_src) load_block(kBlk);
+    __syncthreads();
+    const int4 pure = make_int4(rho0, rho0, rho0, rho0);
+    int qb = -2, par = 0;
+    for (int rb = 0; rb < n_src; rb += kBlk, qb += kBlk, par ^= 1) {
+        const int nb = min(kBlk, n_src - rb);
+        int* cnt = cnt2 + 4 * par;
+        // b. scatter of block rb; the counters of block rb + 4 are cleared meanwhile
+        const int n0 = cnt[0], n1 = cnt[1], n2 = cnt[2], n3 = cnt[3];
+        if (tid < 4) cnt2[4 * (par ^ 1) + tid] = 0;
+        if (n0 + n1 <= kStripCap && n2 + n3 <= kStripCap) {
+            const int c0 = (n0 + 31) >> 5, c1 = c0 + ((n1 + 31) >> 5), c2 = c1 + ((n2 + 31) >> 5),
+                      c3 = c2 + ((n3 + 31) >> 5);
+            for (int c = warp; c < c3; c += kStripThreads / 32) {
+                const int lst = c < c0 ? 0 : c < c1 ? 1 : c < c2 ? 2 : 3;      // warp-uniform
+                const int i = 32 * (c - (lst == 0 ? 0 : lst == 1 ? c0 : lst == 2 ? c1 : c2)) + lane;
+                const int n = lst == 0 ? n0 : lst == 1 ? n1 : lst == 2 ? n2 : n3;
+                if (i >= n) continue;
+                const int b = lst >> 1;
+                const uint32_t en = lists[b * kStripCap + ((lst & 1) ? kStripCap - 1 - i : i)];
+                const int4 wa = *(const int4*)cq8[en & 7], wb = *(const int4*)(cq8[en & 7] + 4);
+                const int w[6] = {0, wa.y, wa.z, wa.w, wb.x, wb.y};
+                const uint32_t a = sbuf + 4 * ((en >> 3) & 0xFFFFFu);
+                const uint32_t h = (en >> 23) - 2u;
+                constexpr uint32_t m0 = 4u * (uint32_t)-StMin<0, RW, SLOT>::v, m1 = 4u * (uint32_t)-StMin<1, RW, SLOT>::v;
+                if (lst == 0) fx_own<0, RW, SLOT>(a - m0, w, Seq{});
+                else if (lst == 1) fx_halo<0, RW, SLOT>(a - m0, w, h, (uint32_t)ty, Seq{});
+                else if (lst == 2) fx_own<1, RW, SLOT>(a - m1, w, Seq{});
+                else fx_halo<1, RW, SLOT>(a - m1, w, h, (uint32_t)ty, Seq{});
+            }
+        } else {
+            // direct scatter of the block, one source site per thread and pass
+            const int nsite = nb * (ty + 4) * M2;
+            for (int c = tid; c < nsite; c += kStripThreads) {
+                const int pl = c / ((ty + 4) * M2), rem = c - pl * (ty + 4) * M2, hr = rem / M2, X = rem - hr * M2;
+                uint32_t sp = V.species[((size_t)wrap(z0 - 2 + rb + pl) * L + wrap(y0 - 2 + hr)) * M2 + X];
+                if (sp == 0) continue;
+                sp = sp > 7 ? 7 : sp;
+                const int bb = X & 1, u = (pl + 2) * SLOT + hr * RW + X + kRowPad;
+                for (int k = 0; k < kSph; ++k) {
+                    const int o = sph[k];
+                    const int dyc = half_floor(bb + off_dy(o)), dzc = half_floor(bb + off_dz(o));
+                    if ((unsigned)(hr + dyc - 2) < (unsigned)ty)
+                        atomicAdd(buf + u + dzc * SLOT + dyc * RW + off_dx(o), cq8[sp][off_extra(o)]);
+                }
+            }
+        }
+        __syncthreads();
+        // c. planes 0..3 are complete: row pads folded into the row ends, 16-byte
+        // stores (planes outside the CTA's z range dropped); planes 4..7 move down
+        // (pads included) and restart as pure Fe.  The next block's lists are built
+        // in the same phase.
+#pragma unroll 1
+        for (int i = 0; i < kBlk; ++i) {
+            const int q = qb + i;
+            const bool wr = q >= 2 && q < tz + 2;
+            int4* out = (int4*)(V.rho + ((size_t)(z0 + q - 2) * L + y0) * M2);
+            for (int r = warp; r < ty; r += kStripThreads / 32) {
+                int32_t* rowi = buf + i * SLOT + (r + kGuard) * RW + kRowPad;
+                int32_t* upi = rowi + kBlk * SLOT;
+                int4* row = (int4*)rowi;
+                int4* up = (int4*)upi;
+                int4* orow = out + r * nq;
+                for (int c = lane; c < nq; c += 32) {
+                    int4 val = row[c];
+                    if (c == 0) {             // right pads (X = 2L .. 2L+2) into sites 0..2
+                        val.x += rowi[M2];
+                        val.y += rowi[M2 + 1];
+                        val.z += rowi[M2 + 2];
+                        row[nq] = up[nq];
+                        up[nq] = make_int4(0, 0, 0, 0);
+                    }
+                    if (c == nq - 1) {        // left pads (X = -3 .. -1) into sites 2L-3 .. 2L-1
+                        val.y += rowi[-3];
+                        val.z += rowi[-2];
+                        val.w += rowi[-1];
+                        row[-1] = up[-1];
+                        up[-1] = make_int4(0, 0, 0, 0);
+                    }
+                    if (wr) __stcs(orow + c, val);
+                    row[c] = up[c];
+                    up[c] = pure;
+                }
+            }
+        }
+        if (rb + kBlk < n_src) {
+            append(rb + kBlk, cnt2 + 4 * (par ^ 1));
+            if (rb + 2 * kBlk < n_src) load_block(rb + 2 * kBlk);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kStripThreads, 2) density_strip_kernel(const VoxelDev* vox, const ModelDev* M,
                                                                          const Tables* tab, const int4* items) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int4 s_wt[8][8][2];      // [species][sub]: f_s - f_Fe at the 8 offsets k = sub + 8j
+    __shared__ __align__(16) int32_t s_cq8[8][8];   // [species][shell]: f_s - f_Fe (0 for Fe and codes > 4)
     __shared__ int32_t s_sph[64];
-    __shared__ int s_count[4];
+    __shared__ int s_count[8];
     const int4 it = items[blockIdx.x];
     const int tid = threadIdx.x;
     if (tid < kSph) s_sph[tid] = tab->sph_off[tid];
+    if (tid < 64) s_cq8[tid >> 3][tid & 7] = (tid >> 3) >= 1 && (tid >> 3) <= 4 ? M->cq[tid >> 3][tid & 7] : 0;
     __syncthreads();
+    const VoxelDev& V = vox[it.x];
+    const int L = V.L;
+    int32_t* buf = (int32_t*)sm;
+    if (((it.w >> 16) & 1) && L <= 128) {
+        const int LG = strip_geom_L(L);
+        uint32_t* lists = (uint32_t*)(sm + sizeof(int32_t) * (size_t)kPlanes * strip_slot(strip_rows(L), LG));
+        if (LG == 32)
+            strip_fast<32, 16>(V, it, buf, lists, s_cq8, s_sph, s_count, M->rho_pure);
+        else if (LG == 64)
+            strip_fast<64, 16>(V, it, buf, lists, s_cq8, s_sph, s_count, M->rho_pure);
+        else
+            strip_fast<128, 8>(V, it, buf, lists, s_cq8, s_sph, s_count, M->rho_pure);
+        return;
+    }
     for (int i = tid; i < 8 * 8 * 8; i += kStripThreads) {
         const int sp = i >> 6, sub = (i >> 3) & 7, j = i & 7, k = sub + 8 * j;
         ((int32_t*)s_wt)[i] = (sp >= 1 && sp <= 4 && k < kSph) ? M->cq[sp][off_extra(s_sph[k])] : 0;
     }
     __syncthreads();
-    const VoxelDev& V = vox[it.x];
     const int TY = it.w >> 17;
-    int32_t* buf = (int32_t*)sm;
-    uint32_t* lists = (uint32_t*)(sm + sizeof(int32_t) * (size_t)kPlanes * strip_slot(TY, V.L));
+    uint32_t* lists = (uint32_t*)(sm + sizeof(int32_t) * (size_t)kPlanes * strip_slot(TY, L));
     if ((it.w >> 16) & 1)
         strip_body<true>(V, it, buf, lists, s_wt, s_sph, s_count, M->rho_pure);
     else
@@ -434,7 +682,9 @@ __global__ void __launch_bounds__(kStripThreads, 2) density_strip_kernel(const V
 }
 
 int density_strip_rows(int L) { return strip_rows(L); }
-size_t density_strip_smem(int L) { return strip_smem(strip_rows(L), L); }
+// a 16-byte strip of L <= 128 takes the fixed geometry of strip_geom_L(L), which
+// holds the byte path's layout too
+size_t density_strip_smem(int L) { return strip_smem(strip_rows(L), L <= 128 ? strip_geom_L(L) : L); }
 
 cudaError_t launch_density(const VoxelDev* vox, const ModelDev* M, const Tables* tab, const int4* tiles,
                            int n_tiles, const int4* strips, int n_strips, size_t strip_dyn, cudaStream_t st) {
