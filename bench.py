@@ -226,6 +226,9 @@ def main():
     ap.add_argument("--large-run", action="store_true",
                     help="run the large configuration as configured (128^3 cells, 64 vacancies, 1e8 events, "
                          "Cu-cluster histogram every 1e6 events) and print its JSON")
+    ap.add_argument("--large-events", type=int, default=100_000_000, help="events of --large-run")
+    ap.add_argument("--large-every", type=int, default=1_000_000,
+                    help="events between Cu-cluster histograms in --large-run (one step launch each)")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload (Poisson arrivals, continuous batching) instead")
     args = ap.parse_args()
@@ -244,7 +247,8 @@ def main():
         import torch
         from paper_2604_24091_gb300 import Batch
         torch.cuda.set_device(0)
-        print(json.dumps(large_run(synth.default_model(), torch, Batch)), flush=True)
+        print(json.dumps(large_run(synth.default_model(), torch, Batch, args.large_events, args.large_every)),
+              flush=True)
         return
     if args.sublattice:
         import torch
